@@ -1,0 +1,173 @@
+/*
+ * mf.h -- C interface of the GB300 (sm_103a) library for the FFT-based method-of-lines
+ * solution of thin-film (2D) and bulk (3D) magnetization problems of type-II
+ * superconductors, after L. Prigozhin and V. Sokolovsky, "FFT-based solution of 2D and 3D
+ * magnetization problems in type-II superconductivity" (arXiv:1801.04869).
+ *
+ * All quantities are dimensionless as in Section 2.3 (film: lengths / l, t / t0,
+ * e / e0, j / jc, h_z / jc, g / (jc l), t0 = mu0 jc l / e0) and Section 3.2, Eq. 19 (bulk:
+ * h / (jc l), t0 = mu0 jc l^2 / e0), so mu0 = 1; e0 and jc default to 1.
+ *
+ * Grid: nx x ny (x nz) cells, cell-centred, on the periodic box
+ * D = [-Lx, Lx] x [-Ly, Ly] (x [-Lz, Lz]) (Section 2.2, Section 3.1); x is the fastest
+ * index.  Each extent must be a power of two: film 8..2048 per axis, bulk 8..512 per axis.
+ *
+ * State vectors (device, float64):
+ *   film  g, the stream function of the sheet current (Eq. 2), nx*ny values
+ *   bulk  h, the magnetic field, 3*nx*ny*nz values, component-major (h_x block, h_y, h_z)
+ *
+ * Ownership: the caller owns every device buffer it passes, including the workspace
+ * (mf_workspace_bytes() bytes, 256-byte aligned).  The problem handle is host memory owned by
+ * the library until mf_destroy().  No call allocates device memory.  All work is queued on
+ * the stream given to mf_create(); calls that return a status synchronise that stream.
+ *
+ * Errors: every call returns an mf_status; no C++ exception crosses this interface.
+ * mf_last_error() gives a message for the most recent failing call on a handle.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_ARG = 1,             /* invalid argument or unsupported size */
+  MF_ERR_CUDA = 2,            /* a CUDA call failed (message in mf_last_error) */
+  MF_ERR_NOCONV = 3,          /* outside iteration did not reach iter_tol in iter_max steps */
+  MF_ERR_NONFINITE = 4,       /* a NaN or infinity appeared in a derivative */
+  MF_ERR_STEP_UNDERFLOW = 5,  /* adaptive step fell below h_min */
+  MF_ERR_WORKSPACE = 6,       /* workspace too small or misaligned */
+  MF_ERR_BARRIER = 7          /* a grid barrier timed out; the launch stopped early */
+} mf_status;
+
+typedef struct mf_problem mf_problem;
+
+/* Problem description.  Fill with mf_default_params() first. */
+typedef struct {
+  int dim;                    /* 2 = thin film (state g), 3 = bulk (state h) */
+  int nx, ny, nz;             /* grid; nz = 1 for a film */
+  double Lx, Ly, Lz;          /* half extents of D */
+  const uint8_t* mask;        /* host, nx*ny*nz: 0 = free space (Ohm law rho_out, the outside
+                                 iteration acts here), 1 = superconductor (power law),
+                                 2 = normal conductor, Ohm law, not iterated (filled hole in a
+                                 film, Section 2.2; cutting layer in a bulk body, Section 3.1) */
+  const double* jc_map;       /* host, nx*ny*nz critical current per cell, or NULL (use jc) */
+  double jc, n, e0;           /* power law rho = (e0/jc) |j/jc|^(n-1), Eq. 3 / Eq. 13 */
+  double rho_out;             /* fictitious resistivity of free space and normal cells */
+  double sigma;               /* Gaussian filter width; <= 0: sqrt(dx^2+dy^2(+dz^2)) */
+  double lambda;              /* film relaxation of Eq. 12 (0.7, Section 2.2) */
+  double iter_tol;            /* film: absolute bound on mean |g_dot| over free space
+                                 (2e-4, Section 2.3); bulk: delta_it of Section 3.1.
+                                 <= 0: run exactly iter_max iterations */
+  int iter_max;               /* cap on outside iterations per right-hand side */
+  int precision;              /* 0: FP64 transforms; 1: FP32 transforms and power law with
+                                 FP64 state, error norm and iteration residual */
+  double rtol, atol;          /* BS23 tolerances */
+  double h0;                  /* first step; <= 0: min(1e-3, 0.01 (t1 - t0)) */
+  double h_min;               /* smallest step before MF_ERR_STEP_UNDERFLOW */
+  const double* he_t;         /* host, he_knots increasing times of a piecewise-linear h_e(t) */
+  const double* he_v;         /* host, values at the knots */
+  int he_knots;               /* 0: use the sinusoid below */
+  double he_sin_amp, he_sin_period;   /* h_e = amp sin(2 pi t / period) */
+  double he_dir[3];           /* bulk: direction of the uniform applied field (default z) */
+} mf_params;
+
+/* One attempted BS23 step (lock-step log). */
+typedef struct {
+  double t, h, t_new, err;
+  int outcome;                /* 0 rejected (error), 1 accepted, 2 rejected (iteration failed) */
+  int iters[4];               /* outside iterations of stages k1..k4, -1 if not evaluated */
+  int pad;
+} mf_step_log;
+
+/* Counters and integrator state. */
+typedef struct {
+  double t, h;
+  long long n_attempts, n_accepted, n_rejected, n_rhs, n_iters, n_noconv, log_count;
+  int last_iters;
+  double last_r, last_err;
+  int grid, threads, smem_bytes, rows_per_item;
+  long long workspace_used;
+} mf_info;
+
+enum { MF_READ_HZ = 0, MF_READ_MOMENT = 1, MF_READ_J = 2 };
+
+/* Defaults: dim 2, n 19, jc = e0 = 1, rho_out 1, lambda 0.7, iter_tol 2e-4, iter_max 1000,
+   precision 0, rtol = atol = 1e-6, h_min 1e-12, he_dir (0,0,1). */
+void mf_default_params(mf_params* p);
+
+/* Device workspace needed by mf_create for these parameters (0 if they are invalid). */
+size_t mf_workspace_bytes(const mf_params* p);
+
+/* Set up a problem in a caller-owned device workspace: copies the mask, jc map, knots and
+   transform tables, and precomputes the free-space responses used by the outside iteration.
+   `stream` is a cudaStream_t (NULL = legacy default stream).  The integrator starts at t = 0
+   with a zero state; use mf_set_state() to change it. */
+mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* stream,
+                    mf_problem** out);
+
+/* One right-hand side f(t, y) (Section 2.2 for films: Eqs. 9-12; Section 3.1 for bulk
+   bodies: Eqs. 13-18).  d_y and d_ydot are device float64 state vectors.  The outside
+   iteration starts from the free-space solution of the previous call (warm start, Section
+   2.2) and updates it.  Returns MF_ERR_NOCONV when the iteration did not converge (d_ydot then
+   holds the last iterate).  *iters_out (may be NULL) receives the number of iterations. */
+mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, int* iters_out);
+
+/* As mf_rhs, with an explicit h_e segment (-2: from t) and, when force_iters > 0, exactly
+   force_iters outside iterations (for lock-step comparison with another implementation). */
+mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double* d_ydot,
+                    int force_iters, int* iters_out);
+
+/* Forget the warm start: the next right-hand side starts from h_e_dot on free space. */
+mf_status mf_reset_warm(mf_problem* pb);
+
+/* Set the integrator state: time t, next step h (<= 0: default), state d_y (device, copied).
+   Clears the first-same-as-last derivative and the step log. */
+mf_status mf_set_state(mf_problem* pb, double t, double h, const double* d_y);
+
+/* Copy the current state to d_y (device, may be NULL) and return t and h. */
+mf_status mf_get_state(mf_problem* pb, double* t, double* h, double* d_y);
+
+/* Advance with adaptive BS23 steps until t reaches t_target exactly or max_attempts step
+   attempts were made (one launch; every decision is taken on the device).  Steps are
+   clipped to end on t_target and on h_e knots. */
+mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts);
+
+/* One BS23 step attempt towards t_max; *accepted (may be NULL) is 1 if it was accepted. */
+mf_status mf_step(mf_problem* pb, double t_max, int* accepted);
+
+/* Integrate from the current state to each time in t_out (increasing) and record readouts:
+   h_m_out (host, may be NULL) gets the magnetization (film: m_z, 1 value per time; bulk:
+   m, 3 values per time); d_hz_out (device, may be NULL) gets h_z (film) or j (bulk, 3 fields)
+   per output time. */
+mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_m_out,
+                      double* d_hz_out);
+
+/* Readout of the current state: MF_READ_HZ (film: h_z = h_e + F^-1[(|k|/2) F g], end of
+   Section 2.1; nx*ny values), MF_READ_MOMENT (film: m_z = integral of g; bulk:
+   m = 1/2 integral of r x j over the conductor; 1 or 3 values), MF_READ_J (bulk:
+   j = curl h, 3 fields).  d_out is device memory, except for MF_READ_MOMENT where it is host
+   memory. */
+mf_status mf_readout(mf_problem* pb, int what, double* out);
+
+/* Same readouts of an arbitrary device state vector d_y at time t. */
+mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, double* out);
+
+/* Counters, state and launch configuration. */
+mf_status mf_get_info(mf_problem* pb, mf_info* out);
+
+/* Copy up to cap logged step attempts (host memory); *count gets the number logged. */
+mf_status mf_get_log(mf_problem* pb, mf_step_log* out, long long cap, long long* count);
+
+const char* mf_last_error(const mf_problem* pb);
+void mf_destroy(mf_problem* pb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

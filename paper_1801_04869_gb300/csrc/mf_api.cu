@@ -1,0 +1,525 @@
+// Host side of the C interface declared in include/mf.h: parameter checks, the workspace
+// layout, transform tables, and the launches of the persistent kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mf.h"
+#include "mf_common.cuh"
+
+using namespace mf;
+
+struct mf_problem {
+  mf_params p;
+  Desc d;
+  cudaStream_t stream;
+  int device;
+  char* ws;
+  size_t ws_bytes;
+  size_t used;
+  double* scratch_m;            // device scalar(s) for moment readouts (in the workspace)
+  std::string err;
+  bool have_knots;
+};
+
+namespace {
+
+constexpr long long LOG_CAP = 1 << 16;
+constexpr int NSLOTS = 8;
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t Sa, Sb, hd, u, q1, q2, jc, mask, twx, twy, twz, ktab, gtab, fbuf[6], partials, st, gb,
+      log, knots, mscr, total;
+  long long ncell, nspec, nstate;
+  int max_items;
+};
+
+mf_status check_params(const mf_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return MF_ERR_ARG; }
+  if (p->dim != 2 && p->dim != 3) { why = "dim must be 2 or 3"; return MF_ERR_ARG; }
+  const int nz = p->dim == 2 ? 1 : p->nz;
+  if (!is_pow2(p->nx) || !is_pow2(p->ny) || !is_pow2(nz)) { why = "grid extents must be powers of two"; return MF_ERR_ARG; }
+  if (p->dim == 2) {
+    if (p->nx < 8 || p->ny < 8 || p->nx > 2048 || p->ny > 2048) { why = "film grid must be 8..2048 per axis"; return MF_ERR_ARG; }
+    if (p->nz != 1) { why = "film needs nz = 1"; return MF_ERR_ARG; }
+  } else {
+    if (p->nx < 8 || p->ny < 8 || nz < 8 || p->nx > 512 || p->ny > 512 || nz > 512) { why = "bulk grid must be 8..512 per axis"; return MF_ERR_ARG; }
+  }
+  if (!(p->Lx > 0) || !(p->Ly > 0) || (p->dim == 3 && !(p->Lz > 0))) { why = "half extents must be positive"; return MF_ERR_ARG; }
+  if (!p->mask) { why = "mask is NULL"; return MF_ERR_ARG; }
+  if (!(p->n >= 1) || !(p->jc > 0) || !(p->e0 > 0) || !(p->rho_out >= 0)) { why = "need n >= 1, jc > 0, e0 > 0, rho_out >= 0"; return MF_ERR_ARG; }
+  if (p->iter_max < 1) { why = "iter_max must be >= 1"; return MF_ERR_ARG; }
+  if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return MF_ERR_ARG; }
+  if (p->he_knots < 0 || (p->he_knots > 0 && (!p->he_t || !p->he_v))) { why = "bad h_e knots"; return MF_ERR_ARG; }
+  for (int i = 1; i < p->he_knots; ++i)
+    if (!(p->he_t[i] > p->he_t[i - 1])) { why = "h_e knot times must increase"; return MF_ERR_ARG; }
+  if (p->he_knots == 0 && !(p->he_sin_period > 0)) { why = "sinusoid period must be positive"; return MF_ERR_ARG; }
+  if (!(p->rtol >= 0) || !(p->atol > 0)) { why = "need rtol >= 0 and atol > 0"; return MF_ERR_ARG; }
+  return MF_OK;
+}
+
+Layout layout(const mf_params* p) {
+  Layout L{};
+  const int nz = p->dim == 2 ? 1 : p->nz;
+  const size_t ts = p->precision ? 4 : 8;
+  const int ncomp = p->dim == 2 ? 1 : 3;
+  L.ncell = (long long)p->nx * p->ny * nz;
+  L.nspec = (long long)(p->nx / 2 + 1) * p->ny * nz;
+  L.nstate = L.ncell * ncomp;
+  L.max_items = (int)(p->dim == 2 ? p->ny : (long long)p->ny * nz);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  L.Sa = take(3 * L.nspec * 2 * ts);
+  L.Sb = take(3 * L.nspec * 2 * ts);
+  L.hd = take(ncomp * L.ncell * ts);
+  L.u = take(p->dim == 2 ? L.ncell * ts : 0);
+  L.q1 = take(p->dim == 2 ? L.ncell * ts : 0);
+  L.q2 = take(p->dim == 2 ? L.ncell * ts : 0);
+  L.jc = take(p->jc_map ? L.ncell * ts : 0);
+  L.mask = take(L.ncell);
+  L.twx = take(p->nx * 2 * ts);
+  L.twy = take(p->ny * 2 * ts);
+  L.twz = take(nz * 2 * ts);
+  const int nk = p->nx / 2 + 1 + p->ny + nz;
+  L.ktab = take(nk * ts);
+  L.gtab = take(nk * ts);
+  for (int i = 0; i < 6; ++i) L.fbuf[i] = take(L.nstate * 8);
+  L.partials = take((size_t)NSLOTS * L.max_items * 8);
+  L.st = take(sizeof(SolverState));
+  L.gb = take(sizeof(GridBarrier));
+  L.log = take(LOG_CAP * sizeof(StepLog));
+  L.knots = take(2 * (size_t)(p->he_knots > 0 ? p->he_knots : 1) * 8);
+  L.mscr = take(8 * 8);
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+void fill_tables(const mf_params* p, double sigma, std::vector<char>& tw, std::vector<char>& kt,
+                 std::vector<char>& gt) {
+  const int nz = p->dim == 2 ? 1 : p->nz;
+  const int ns[3] = {p->nx, p->ny, nz};
+  std::vector<T> t;
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < ns[a]; ++j) {
+      const double ang = -2.0 * M_PI * (double)j / (double)ns[a];
+      t.push_back((T)std::cos(ang));
+      t.push_back((T)std::sin(ang));
+    }
+  tw.assign((const char*)t.data(), (const char*)(t.data() + t.size()));
+  std::vector<T> k, g;
+  const double Ls[3] = {p->Lx, p->Ly, p->dim == 2 ? 1.0 : p->Lz};
+  for (int a = 0; a < 3; ++a) {
+    const int n = ns[a];
+    const int cnt = a == 0 ? n / 2 + 1 : n;
+    for (int i = 0; i < cnt; ++i) {
+      int m = i < n / 2 ? i : i - n;     // FFT order; index n/2 is the Nyquist m = -n/2
+      if (a == 0 && i == n / 2) m = -n / 2;
+      const double kv = M_PI * (double)m / Ls[a];
+      k.push_back((T)kv);
+      g.push_back((T)std::exp(-kv * kv * sigma * sigma / 2.0));
+    }
+  }
+  kt.assign((const char*)k.data(), (const char*)(k.data() + k.size()));
+  gt.assign((const char*)g.data(), (const char*)(g.data() + g.size()));
+}
+
+mf_status cuda_fail(mf_problem* pb, cudaError_t e, const char* what) {
+  if (pb) pb->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return MF_ERR_CUDA;
+}
+
+#define MF_CUDA(pb, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(pb, e_, #call); \
+  } while (0)
+
+mf_status read_state(mf_problem* pb, SolverState* s) {
+  MF_CUDA(pb, cudaMemcpyAsync(s, pb->d.st, sizeof(SolverState), cudaMemcpyDeviceToHost, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  return MF_OK;
+}
+mf_status write_state(mf_problem* pb, const SolverState* s) {
+  MF_CUDA(pb, cudaMemcpyAsync(pb->d.st, s, sizeof(SolverState), cudaMemcpyHostToDevice, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  return MF_OK;
+}
+
+mf_status launch(mf_problem* pb, const KernelArgs& a) {
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  MF_CUDA(pb, cudaMemsetAsync(pb->d.gb, 0, sizeof(GridBarrier), pb->stream));
+  cudaError_t e = pb->d.dim == 2 ? film_launch(pb->d.precision, pb->d, a, pb->stream)
+                                 : bulk_launch(pb->d.precision, pb->d, a, pb->stream);
+  if (e != cudaSuccess) return cuda_fail(pb, e, "persistent kernel launch");
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  if (s.status != ST_OK) {
+    static const char* names[] = {"ok", "argument", "cuda", "outside iteration did not converge",
+                                  "non-finite derivative", "step size underflow", "workspace",
+                                  "grid barrier timed out"};
+    pb->err = names[s.status >= 0 && s.status <= 7 ? s.status : 0];
+    return (mf_status)s.status;
+  }
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_default_params(mf_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->nz = 1;
+  p->jc = 1.0; p->n = 19.0; p->e0 = 1.0; p->rho_out = 1.0; p->sigma = 0.0;
+  p->lambda = 0.7; p->iter_tol = 2e-4; p->iter_max = 1000;
+  p->precision = 0;
+  p->rtol = 1e-6; p->atol = 1e-6; p->h0 = 0.0; p->h_min = 1e-12;
+  p->he_sin_amp = 0.0; p->he_sin_period = 1.0;
+  p->he_dir[0] = 0.0; p->he_dir[1] = 0.0; p->he_dir[2] = 1.0;
+}
+
+size_t mf_workspace_bytes(const mf_params* p) {
+  std::string why;
+  if (check_params(p, why) != MF_OK) return 0;
+  return layout(p).total;
+}
+
+mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* stream,
+                    mf_problem** out) {
+  if (!out) return MF_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  mf_status cs = check_params(p, why);
+  if (cs != MF_OK) return cs;
+  const Layout L = layout(p);
+  if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255)) return MF_ERR_WORKSPACE;
+
+  mf_problem* pb = new mf_problem();
+  pb->p = *p;
+  pb->stream = (cudaStream_t)stream;
+  pb->ws = (char*)d_workspace;
+  pb->ws_bytes = bytes;
+  pb->used = L.total;
+  if (cudaGetDevice(&pb->device) != cudaSuccess) { delete pb; return MF_ERR_CUDA; }
+
+  const int nz = p->dim == 2 ? 1 : p->nz;
+  Desc& d = pb->d;
+  std::memset(&d, 0, sizeof(d));
+  d.dim = p->dim; d.nx = p->nx; d.ny = p->ny; d.nz = nz; d.precision = p->precision;
+  d.lgx = ilog2(p->nx); d.lgy = ilog2(p->ny); d.lgz = ilog2(nz);
+  d.Lx = p->Lx; d.Ly = p->Ly; d.Lz = p->dim == 2 ? 0.0 : p->Lz;
+  d.dx = 2 * p->Lx / p->nx; d.dy = 2 * p->Ly / p->ny; d.dz = p->dim == 2 ? 0.0 : 2 * p->Lz / nz;
+  const double s2 = d.dx * d.dx + d.dy * d.dy + d.dz * d.dz;
+  d.sigma = p->sigma > 0 ? p->sigma : std::sqrt(s2);   // Section 2.2 / Section 3.2 choice
+  d.n = p->n; d.e0 = p->e0; d.jc = p->jc; d.rho_out = p->rho_out; d.lam = p->lambda;
+  d.iter_tol = p->iter_tol; d.iter_max = p->iter_max;
+  d.rtol = p->rtol; d.atol = p->atol; d.h_min = p->h_min;
+  d.he_knots = p->he_knots; d.he_sin_amp = p->he_sin_amp; d.he_sin_period = p->he_sin_period;
+  for (int i = 0; i < 3; ++i) d.he_dir[i] = p->he_dir[i];
+  d.ncell = L.ncell; d.nspec = L.nspec;
+  long long nout = 0;
+  for (long long i = 0; i < L.ncell; ++i) nout += p->mask[i] == 0;
+  for (long long i = 0; i < L.ncell; ++i)
+    if (p->mask[i] > 2) { delete pb; return MF_ERR_ARG; }
+  d.nout = nout;
+  char* w = pb->ws;
+  d.Sa = w + L.Sa; d.Sb = w + L.Sb; d.hd = w + L.hd; d.u = w + L.u; d.q1 = w + L.q1; d.q2 = w + L.q2;
+  d.jcmap = p->jc_map ? (const void*)(w + L.jc) : nullptr;
+  d.mask = (const uint8_t*)(w + L.mask);
+  d.tw_x = w + L.twx; d.tw_y = w + L.twy; d.tw_z = w + L.twz;
+  d.ktab = w + L.ktab; d.gtab = w + L.gtab;
+  for (int i = 0; i < 6; ++i) d.fbuf[i] = (double*)(w + L.fbuf[i]);
+  d.partials = (double*)(w + L.partials);
+  d.max_items = L.max_items;
+  d.st = (SolverState*)(w + L.st);
+  d.gb = (GridBarrier*)(w + L.gb);
+  d.log = (StepLog*)(w + L.log);
+  d.log_cap = LOG_CAP;
+  d.he_t = (const double*)(w + L.knots);
+  d.he_v = d.he_t + (p->he_knots > 0 ? p->he_knots : 1);
+  pb->scratch_m = (double*)(w + L.mscr);
+
+  // launch configuration: all CTAs co-resident, no more than the widest pass can use
+  const size_t smem = kernel_smem_bytes(p->precision);
+  int per_sm = p->dim == 2 ? film_max_blocks(p->precision, smem) : bulk_max_blocks(p->precision, smem);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pb->device);
+  cudaError_t le = cudaGetLastError();
+  if (per_sm < 1 || nsm < 1 || le != cudaSuccess) {
+    pb->err = "kernel does not fit on this device";
+    delete pb;
+    return MF_ERR_CUDA;
+  }
+  const int coresident = per_sm * nsm;
+  if (p->dim == 2) {
+    int rb1 = std::min(p->ny, 2 * BATCH / p->nx);
+    int rb2 = std::min(p->ny, BATCH / p->nx);
+    const int want = std::max(p->nx / 2 + 1, 1);
+    const int grid = std::min(coresident, want);
+    while (rb1 > 2 && p->ny / rb1 < grid) rb1 /= 2;
+    while (rb2 > 2 && p->ny / rb2 < grid) rb2 /= 2;
+    d.rows_per_item = rb1;
+    d.zs_per_item = rb2;
+    d.grid = std::max(1, std::min(coresident, std::max(want, p->ny / rb1)));
+  } else {
+    // x pass: rb rows of 3 fields; y pass: zs z-lines of 3 fields
+    int rb = std::min(p->ny, 2 * BATCH / (3 * p->nx));
+    rb = std::max(2, rb & ~1);
+    while (rb & (rb - 1)) rb &= rb - 1;
+    int zs = std::min(nz, BATCH / (3 * p->ny));
+    zs = std::max(1, zs);
+    while (zs & (zs - 1)) zs &= zs - 1;
+    const long long xitems = (long long)p->ny * nz / rb;
+    const long long zlines = (long long)(p->nx / 2 + 1) * p->ny;
+    const int grid = (int)std::min<long long>(coresident, std::max(xitems, zlines));
+    while (rb > 2 && (long long)p->ny * nz / rb < grid) rb /= 2;
+    while (zs > 1 && (long long)(p->nx / 2 + 1) * nz / zs < grid) zs /= 2;
+    d.rows_per_item = rb;
+    d.zs_per_item = zs;
+    d.grid = std::max(1, grid);
+    if (3 * p->nx * (rb / 2) > BATCH || 3 * p->ny * zs > BATCH || 3 * nz > BATCH) {
+      pb->err = "grid too large for the shared-memory batch";
+      delete pb;
+      return MF_ERR_ARG;
+    }
+  }
+
+  // tables and inputs
+  std::vector<char> tw, kt, gt;
+  if (p->precision) fill_tables<float>(p, d.sigma, tw, kt, gt);
+  else fill_tables<double>(p, d.sigma, tw, kt, gt);
+  const size_t ts = p->precision ? 4 : 8;
+  std::vector<char> jcbuf;
+  if (p->jc_map) {
+    jcbuf.resize(L.ncell * ts);
+    for (long long i = 0; i < L.ncell; ++i) {
+      if (p->precision) ((float*)jcbuf.data())[i] = (float)p->jc_map[i];
+      else ((double*)jcbuf.data())[i] = p->jc_map[i];
+    }
+  }
+  std::vector<double> knots(2 * (p->he_knots > 0 ? p->he_knots : 1), 0.0);
+  for (int i = 0; i < p->he_knots; ++i) { knots[i] = p->he_t[i]; knots[p->he_knots + i] = p->he_v[i]; }
+  SolverState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.t = 0.0;
+  s0.h = p->h0;
+  s0.ybuf = 0; s0.ynewbuf = 1; s0.k1buf = 2; s0.k4buf = 5;
+  cudaStream_t st = pb->stream;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t n) {
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st);
+  };
+  cp(w + L.mask, p->mask, L.ncell);
+  if (p->jc_map) cp(w + L.jc, jcbuf.data(), jcbuf.size());
+  const size_t twx = p->nx * 2 * ts, twy = p->ny * 2 * ts, twz = nz * 2 * ts;
+  cp(w + L.twx, tw.data(), twx);
+  cp(w + L.twy, tw.data() + twx, twy);
+  cp(w + L.twz, tw.data() + twx + twy, twz);
+  cp(w + L.ktab, kt.data(), kt.size());
+  cp(w + L.gtab, gt.data(), gt.size());
+  cp(w + L.knots, knots.data(), knots.size() * 8);
+  cp(w + L.st, &s0, sizeof(s0));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.fbuf[0], 0, L.nstate * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.hd, 0, (p->dim == 2 ? 1 : 3) * L.ncell * ts, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging buffers die below
+  if (e != cudaSuccess) {
+    cuda_fail(pb, e, "mf_create copies");
+    delete pb;
+    return MF_ERR_CUDA;
+  }
+  if (p->dim == 2) {
+    KernelArgs a{};
+    a.mode = MODE_SETUP;
+    mf_status r = launch(pb, a);
+    if (r != MF_OK) { delete pb; return r; }
+  }
+  *out = pb;
+  return MF_OK;
+}
+
+mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double* d_ydot,
+                    int force_iters, int* iters_out) {
+  if (!pb || !d_y || !d_ydot) return MF_ERR_ARG;
+  KernelArgs a{};
+  a.mode = MODE_RHS; a.t = t; a.y_in = d_y; a.out = d_ydot; a.force_iters = force_iters; a.seg = seg;
+  mf_status r = launch(pb, a);
+  if (iters_out) {
+    SolverState s;
+    if (read_state(pb, &s) == MF_OK) *iters_out = s.last_iters;
+  }
+  return r;
+}
+
+mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, int* iters_out) {
+  return mf_rhs_ex(pb, t, -2, d_y, d_ydot, 0, iters_out);
+}
+
+mf_status mf_reset_warm(mf_problem* pb) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  s.warm_valid = 0;
+  s.A_prev = 0.0;
+  return write_state(pb, &s);
+}
+
+mf_status mf_set_state(mf_problem* pb, double t, double h, const double* d_y) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  s.t = t;
+  s.h = h;
+  s.k1_valid = 0;
+  s.failed = 0;
+  s.log_count = 0;
+  s.status = ST_OK;
+  if (d_y) MF_CUDA(pb, cudaMemcpyAsync(pb->d.fbuf[s.ybuf], d_y, pb->d.ncell * (pb->d.dim == 2 ? 1 : 3) * 8,
+                                       cudaMemcpyDeviceToDevice, pb->stream));
+  return write_state(pb, &s);
+}
+
+mf_status mf_get_state(mf_problem* pb, double* t, double* h, double* d_y) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  if (t) *t = s.t;
+  if (h) *h = s.h;
+  if (d_y) {
+    MF_CUDA(pb, cudaMemcpyAsync(d_y, pb->d.fbuf[s.ybuf], pb->d.ncell * (pb->d.dim == 2 ? 1 : 3) * 8,
+                                cudaMemcpyDeviceToDevice, pb->stream));
+    MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  }
+  return MF_OK;
+}
+
+static mf_status ensure_h(mf_problem* pb, double t_target) {
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  if (!(s.h > 0)) {
+    s.h = std::min(1e-3, 0.01 * (t_target - s.t));
+    if (!(s.h > 0)) s.h = 1e-3;
+    return write_state(pb, &s);
+  }
+  return MF_OK;
+}
+
+mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {
+  if (!pb) return MF_ERR_ARG;
+  mf_status r = ensure_h(pb, t_target);
+  if (r != MF_OK) return r;
+  KernelArgs a{};
+  a.mode = MODE_ADVANCE; a.t_target = t_target; a.max_attempts = max_attempts;
+  return launch(pb, a);
+}
+
+mf_status mf_step(mf_problem* pb, double t_max, int* accepted) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s0;
+  mf_status r = read_state(pb, &s0);
+  if (r != MF_OK) return r;
+  r = mf_advance(pb, t_max, 1);
+  if (accepted) {
+    SolverState s1;
+    if (read_state(pb, &s1) == MF_OK) *accepted = s1.n_accepted > s0.n_accepted;
+  }
+  return r;
+}
+
+mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, double* out) {
+  if (!pb || !d_y || !out) return MF_ERR_ARG;
+  KernelArgs a{};
+  a.t = t; a.y_in = d_y;
+  if (what == MF_READ_MOMENT) {
+    a.mode = MODE_MOMENT; a.out = pb->scratch_m;
+    mf_status r = launch(pb, a);
+    if (r != MF_OK) return r;
+    const int nm = pb->d.dim == 2 ? 1 : 3;
+    MF_CUDA(pb, cudaMemcpyAsync(out, pb->scratch_m, nm * 8, cudaMemcpyDeviceToHost, pb->stream));
+    MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+    return MF_OK;
+  }
+  if (what == MF_READ_HZ && pb->d.dim == 2) { a.mode = MODE_HZ; a.out = out; return launch(pb, a); }
+  if (what == MF_READ_J && pb->d.dim == 3) { a.mode = MODE_J; a.out = out; return launch(pb, a); }
+  pb->err = "readout not available for this dimension";
+  return MF_ERR_ARG;
+}
+
+mf_status mf_readout(mf_problem* pb, int what, double* out) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  return mf_readout_of(pb, what, s.t, pb->d.fbuf[s.ybuf], out);
+}
+
+mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_m_out,
+                      double* d_hz_out) {
+  if (!pb || n_out < 0 || (n_out > 0 && !t_out)) return MF_ERR_ARG;
+  const int nm = pb->d.dim == 2 ? 1 : 3;
+  const long long per = pb->d.dim == 2 ? pb->d.ncell : 3 * pb->d.ncell;
+  for (int k = 0; k < n_out; ++k) {
+    mf_status r = mf_advance(pb, t_out[k], 1LL << 40);
+    if (r != MF_OK) return r;
+    if (h_m_out) {
+      r = mf_readout(pb, MF_READ_MOMENT, h_m_out + (size_t)k * nm);
+      if (r != MF_OK) return r;
+    }
+    if (d_hz_out) {
+      r = mf_readout(pb, pb->d.dim == 2 ? MF_READ_HZ : MF_READ_J, d_hz_out + (size_t)k * per);
+      if (r != MF_OK) return r;
+    }
+  }
+  return MF_OK;
+}
+
+mf_status mf_get_info(mf_problem* pb, mf_info* out) {
+  if (!pb || !out) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  std::memset(out, 0, sizeof(*out));
+  out->t = s.t; out->h = s.h;
+  out->n_attempts = s.n_attempts; out->n_accepted = s.n_accepted; out->n_rejected = s.n_rejected;
+  out->n_rhs = s.n_rhs; out->n_iters = s.n_iters; out->n_noconv = s.n_noconv;
+  out->log_count = s.log_count; out->last_iters = s.last_iters;
+  out->last_r = s.last_r; out->last_err = s.last_err;
+  out->grid = pb->d.grid; out->threads = NT;
+  out->smem_bytes = (int)kernel_smem_bytes(pb->d.precision);
+  out->rows_per_item = pb->d.rows_per_item;
+  out->workspace_used = (long long)pb->used;
+  return MF_OK;
+}
+
+mf_status mf_get_log(mf_problem* pb, mf_step_log* out, long long cap, long long* count) {
+  if (!pb) return MF_ERR_ARG;
+  SolverState s;
+  mf_status r = read_state(pb, &s);
+  if (r != MF_OK) return r;
+  const long long n = std::min(std::min(s.log_count, (long long)LOG_CAP), cap);
+  if (count) *count = s.log_count;
+  static_assert(sizeof(mf_step_log) == sizeof(StepLog), "log layout");
+  if (n > 0 && out) {
+    MF_CUDA(pb, cudaMemcpyAsync(out, pb->d.log, n * sizeof(StepLog), cudaMemcpyDeviceToHost, pb->stream));
+    MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  }
+  return MF_OK;
+}
+
+const char* mf_last_error(const mf_problem* pb) { return pb ? pb->err.c_str() : "null handle"; }
+
+void mf_destroy(mf_problem* pb) { delete pb; }
+
+}  // extern "C"

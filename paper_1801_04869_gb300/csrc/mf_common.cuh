@@ -1,0 +1,252 @@
+// Common device-side types for the FFT method-of-lines kernels (sm_103a).
+//
+// Complex arithmetic, the problem descriptor shared by all phases, the device-resident
+// integrator state, a bounded grid-wide barrier for the persistent cooperative kernels and
+// deterministic block reductions.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mf {
+
+constexpr int NT = 256;           // threads per CTA of the persistent kernels
+constexpr int VPT = 16;           // complex values each thread holds per FFT stage
+constexpr int BATCH = NT * VPT;   // complex points one CTA transforms at once (4096)
+
+// ------------------------------------------------------------------------------------------
+// complex numbers
+// ------------------------------------------------------------------------------------------
+template <typename T> struct C2 { T x, y; };
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ C2<T> cconj(C2<T> a) { return {a.x, -a.y}; }
+template <typename T> __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { return {a.x * s, a.y * s}; }
+// a * (s i) for s = +-1
+template <typename T> __device__ __forceinline__ C2<T> cmul_si(C2<T> a, int s) {
+  return s > 0 ? C2<T>{-a.y, a.x} : C2<T>{a.y, -a.x};
+}
+
+// ------------------------------------------------------------------------------------------
+// status codes (mirrors mf_status of the C interface)
+// ------------------------------------------------------------------------------------------
+enum : int { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_NOCONV = 3, ST_NONFINITE = 4,
+             ST_UNDERFLOW = 5, ST_WORKSPACE = 6, ST_BARRIER = 7 };
+
+// ------------------------------------------------------------------------------------------
+// device-resident solver state (one per problem, in the workspace)
+// ------------------------------------------------------------------------------------------
+struct StepLog {                 // one attempted BS23 step
+  double t, h, t_new, err;
+  int outcome;                   // 0 reject (error), 1 accept, 2 reject (iteration failed)
+  int iters[4];                  // outside iterations of k1..k4, -1 when not evaluated
+  int pad;
+};
+
+struct SolverState {
+  double t, h;
+  double A_prev;                 // shift still to subtract on free space from the warm h_dot (2D)
+  int warm_valid;                // 0: the next call starts from h_e_dot
+  int k1_valid;                  // first-same-as-last derivative available
+  int failed;                    // the previous attempt was rejected
+  int ybuf, ynewbuf, k1buf, k4buf;   // rotation of the FP64 state buffers
+  int status;                    // sticky error status of the last launch
+  int last_iters;                // iterations of the last right-hand side
+  long long n_attempts, n_accepted, n_rejected, n_rhs, n_iters, n_noconv;
+  long long log_count;
+  double last_r;                 // last convergence residual
+  double last_err;
+  double pad[4];
+};
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+  int where;
+};
+
+// ------------------------------------------------------------------------------------------
+// problem descriptor (kernel argument, plain data)
+// ------------------------------------------------------------------------------------------
+struct Desc {
+  int dim, nx, ny, nz;
+  int precision;                 // 0 FP64 transforms, 1 FP32 transforms
+  int lgx, lgy, lgz;
+  double Lx, Ly, Lz, dx, dy, dz;
+  double n, e0, jc, rho_out, sigma, lam, iter_tol;
+  int iter_max;
+  double rtol, atol, h_min;
+  // applied field
+  int he_knots;
+  const double* he_t;
+  const double* he_v;
+  double he_sin_amp, he_sin_period;
+  double he_dir[3];
+  // counts
+  long long ncell;               // nx ny nz
+  long long nout;                // free-space cells
+  long long nspec;               // complex values of one half spectrum ((nx/2+1) ny nz)
+  // device buffers (transform precision T unless noted)
+  void* Sa;                      // spectra, 3 fields
+  void* Sb;                      // spectra, 3 fields (3D: second buffer of the transpose chain)
+  void* hd;                      // h_dot iterate (1 or 3 fields)
+  void* u;                       // raw g_dot (2D)
+  void* q1;                      // F^-1[K1 F(out)] (2D)
+  void* q2;                      // F^-1[K2 F(out)] (2D)
+  const void* jcmap;             // per-cell jc or null
+  const uint8_t* mask;
+  const void* tw_x; const void* tw_y; const void* tw_z;   // twiddle tables exp(-2 pi i j / n)
+  const void* ktab;              // wavenumbers: kx (nx/2+1 values), ky (ny), kz (nz)
+  const void* gtab;              // Gaussian factors exp(-k^2 sigma^2 / 2), same layout
+  double* fbuf[6];               // FP64 state buffers (y, y_new, k1..k4 under rotation)
+  double* partials;              // per-work-item partial reductions
+  int max_items;
+  SolverState* st;
+  GridBarrier* gb;
+  StepLog* log;
+  long long log_cap;
+  int rows_per_item;             // 2D row pass / 3D x pass rows per work item (even)
+  int zs_per_item;               // 3D y pass z-lines per work item
+  int grid;                      // CTAs of the persistent launch
+};
+
+// ------------------------------------------------------------------------------------------
+// bounded grid barrier for cooperative launches.  Every CTA is co-resident (cooperative
+// launch), so the wait ends unless a CTA has already left; a wait that exceeds the time
+// limit raises the abort flag, which every waiter polls, so all CTAs leave promptly.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *(const volatile int*)p;
+}
+
+constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // 4 s per barrier
+
+// returns false when the launch must stop (abort raised)
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks, int where) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int my_gen = ld_acquire_u32(&gb->gen);
+    __threadfence();
+    unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(&gb->gen) == my_gen) {
+        if (ld_volatile_i32(&gb->abort)) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
+          atomicExch(&gb->abort, 1);
+          atomicExch(&gb->where, where);
+          ok = 0;
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+    if (ld_volatile_i32(&gb->abort)) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// deterministic block reductions (fixed tree) of NT values
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// sum over the CTA; result valid in all threads.  `red` holds NT/32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < NT / 32) ? red[l] : 0.0;
+    s = warp_sum(s);
+    if (l == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < NT / 32) ? red[l] : 0.0;
+    s = warp_max(s);
+    if (l == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Sum (or max) of partials[slot * max_items + i] over i < n, in a fixed order, computed
+// identically by every CTA.
+__device__ __forceinline__ double reduce_partials(const double* partials, int max_items, int slot,
+                                                  int n, bool is_max, double* red) {
+  const volatile double* p = partials + (size_t)slot * max_items;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) v = is_max ? fmax(v, p[i]) : v + p[i];
+  return is_max ? block_max(v, red) : block_sum(v, red);
+}
+
+// ------------------------------------------------------------------------------------------
+// launch arguments of the persistent kernels
+// ------------------------------------------------------------------------------------------
+enum Mode { MODE_RHS = 0, MODE_ADVANCE = 1, MODE_HZ = 2, MODE_SETUP = 3, MODE_MOMENT = 4,
+            MODE_J = 5 };
+
+struct KernelArgs {
+  int mode;
+  double t;                   // MODE_RHS / MODE_HZ / MODE_J: time
+  double t_target;            // MODE_ADVANCE
+  long long max_attempts;     // MODE_ADVANCE
+  const double* y_in;         // MODE_RHS / MODE_HZ / MODE_MOMENT / MODE_J input (FP64)
+  double* out;                // MODE_RHS: derivative; MODE_HZ: h_z; MODE_J: j; MODE_MOMENT
+  int force_iters;            // > 0: run exactly this many outside iterations
+  int seg;                    // waveform segment for MODE_RHS (-2: from t)
+};
+
+// launch helpers implemented next to each kernel
+cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s);
+cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s);
+int film_max_blocks(int precision, size_t smem);
+int bulk_max_blocks(int precision, size_t smem);
+size_t kernel_smem_bytes(int precision);
+
+}  // namespace mf

@@ -1,0 +1,115 @@
+// Shared-memory FFT of a batch of lines (Stockham autosort, radix 8 with one radix-4 or
+// radix-2 stage), the building block of every row, column and z pass.
+//
+// A CTA of NT threads transforms `nlines` lines of length L (a power of two, 2..4096) that
+// sit back to back in shared memory, nlines * L <= BATCH.  Stages alternate between two
+// shared buffers (each thread keeps one butterfly in registers).  Twiddles come from a global table
+// tw[m] = exp(-2 pi i m / L) (read-only, cached); the inverse uses their conjugates and is
+// unnormalised.
+#pragma once
+#include "mf_common.cuh"
+
+namespace mf {
+
+template <typename T> struct Sqrt1_2;
+template <> struct Sqrt1_2<float> { static constexpr float v = 0.70710678118654752440f; };
+template <> struct Sqrt1_2<double> { static constexpr double v = 0.70710678118654752440; };
+
+template <typename T, int DIR>
+__device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
+  C2<T> t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+  C2<T> t3 = cmul_si(csub(a1, a3), DIR);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft(C2<T>* v) {
+  if constexpr (R == 2) {
+    C2<T> a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
+    v[0] = a; v[1] = b;
+  } else if constexpr (R == 4) {
+    dft4<T, DIR>(v[0], v[1], v[2], v[3]);
+  } else {
+    // radix-2 decimation in time over two length-4 transforms
+    C2<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C2<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<T, DIR>(e0, e1, e2, e3);
+    dft4<T, DIR>(o0, o1, o2, o3);
+    const T h = Sqrt1_2<T>::v;
+    // W8^1 = (1 + DIR i)/sqrt2, W8^2 = DIR i, W8^3 = (-1 + DIR i)/sqrt2
+    C2<T> w1o = {h * (o1.x - (T)DIR * o1.y), h * (o1.y + (T)DIR * o1.x)};
+    C2<T> w2o = cmul_si(o2, DIR);
+    C2<T> w3o = {h * (-o3.x - (T)DIR * o3.y), h * (-o3.y + (T)DIR * o3.x)};
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, w1o); v[5] = csub(e1, w1o);
+    v[2] = cadd(e2, w2o); v[6] = csub(e2, w2o);
+    v[3] = cadd(e3, w3o); v[7] = csub(e3, w3o);
+  }
+}
+
+// one Stockham stage of radix R from `in` to `out`; p = 2^lgp = product of the radices
+// already applied.  Butterfly b of line `line` reads in[i + j L/R] (j < R), multiplies by
+// w^(j k) with k = i mod p and w = exp(DIR 2 pi i / (p R)), and writes its length-R DFT to
+// out[(i - k) R + k + j p].
+template <typename T, int R, int LGR, int DIR>
+__device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, int lgp, int nlines,
+                                          const C2<T>* __restrict__ tw) {
+  const int lgq = lgL - LGR;          // log2(L / R)
+  const int q = 1 << lgq;
+  const int p = 1 << lgp;
+  const int nb = nlines << lgq;       // butterflies in this stage
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int line = b >> lgq, i = b & (q - 1);
+    const int k = i & (p - 1);
+    const C2<T>* src = in + (line << lgL) + i;
+    C2<T> v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = src[j << lgq];
+    if (lgp > 0) {
+      // w^(j k) = tw[j k L / (p R)] (conjugated for DIR > 0)
+      const int step = k << (lgL - lgp - LGR);
+#pragma unroll
+      for (int j = 1; j < R; ++j) {
+        C2<T> w = tw[j * step];
+        if (DIR > 0) w.y = -w.y;
+        v[j] = cmul(v[j], w);
+      }
+    }
+    dft<T, R, DIR>(v);
+    C2<T>* dst = out + (line << lgL) + ((i - k) << LGR) + k;
+#pragma unroll
+    for (int j = 0; j < R; ++j) dst[j << lgp] = v[j];
+  }
+  __syncthreads();
+}
+
+// FFT of nlines lines of length 2^lgL held in shared buffer `a`, using `b` as the second
+// buffer of the autosort; returns the buffer that holds the result (a or b).  Must be called
+// by all NT threads of the CTA (it synchronises).
+template <typename T, int DIR>
+__device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines,
+                                         const C2<T>* __restrict__ tw) {
+  int lgp = 0;
+  int rem = lgL;
+  C2<T>* in = a;
+  C2<T>* out = b;
+  while (rem > 0) {
+    if (rem >= 3) {
+      fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw);
+      lgp += 3; rem -= 3;
+    } else if (rem == 2) {
+      fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw);
+      lgp += 2; rem -= 2;
+    } else {
+      fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw);
+      lgp += 1; rem -= 1;
+    }
+    C2<T>* t = in; in = out; out = t;
+  }
+  return in;
+}
+
+}  // namespace mf

@@ -1,0 +1,648 @@
+// Thin-film (2D) right-hand side and BS23 integrator as one persistent cooperative kernel.
+//
+// Method: Section 2 of Prigozhin & Sokolovsky (arXiv:1801.04869).  One right-hand side
+// f(t, g) runs, as phases separated by grid barriers:
+//   P1  x pass of the stage input g_s = y + h sum a_j k_j           -> Sa
+//   P2  y pass: smoothed gradient  i k_{x,y} G                         (Section 2.2)
+//   P3  x pass: j = (g_y, -g_x) (Eq. 2), e = rho(|j|) j (Eq. 3), forward x pass of e -> Sb
+//   P4  y pass: -curl e = -i G (k_x e_y - k_y e_x)                     (Eq. 4 / Eq. 9)
+//   P5  x pass: h_dot_in on the conductor, warm h_dot on free space, sum for A (Eq. 10)
+//   loop (Eqs. 11-12):
+//   P6  y pass: 2/|k|
+//   P7  x pass: u = raw - A q1, sum over free space (C), forward of mask_out u
+//   P8  residual r = mean_out |u - C| (stop test, Section 2.3)
+//   P9  y pass: lambda (|k|/2) G
+//   P10 x pass: h_dot_out <- h_dot_out - A - (w - C q2), sum for the next A, forward
+//   end: g_dot = (u - C) on the conductor, 0 on free space (FP64)
+// The constants A and C are applied through the precomputed fields q1 = F^-1[K1 F(out)] and
+// q2 = F^-1[K2 F(out)], which is exact by linearity and saves one pass per iteration.
+#include "mf_passes.cuh"
+
+namespace mf {
+
+constexpr double PI_D = 3.14159265358979323846;
+
+enum Op2 { OP_GRAD = 0, OP_CURLNEG = 1, OP_K1 = 2, OP_K2 = 3, OP_KH = 4, OP_ID = 5 };
+
+// stage input y + sum c_j k_j (FP64), optionally written to ynew
+struct StageIn {
+  const double* y;
+  int nk;
+  double c[3];
+  const double* k[3];
+  double* ynew;
+};
+
+// per-CTA copy of the scalars every CTA agrees on
+struct Shared {
+  double red[NT / 32];
+  double A, C, r, hed;
+  int warm_valid;
+  double A_prev;
+};
+
+template <typename T>
+struct Film {
+  const Desc& d;
+  C2<T>* sm;         // shared buffer A (BATCH values)
+  C2<T>* sm2;        // shared buffer B
+  Shared& sh;
+  int nx, ny, lgx, lgy, half, nkx;
+  long long nspec, ncell;
+  C2<T>* Sa;
+  C2<T>* Sb;
+  T* hd;
+  T* u;
+  const T* q1;
+  const T* q2;
+  const uint8_t* mask;
+  const T* jcmap;
+  const C2<T>* twx;
+  const C2<T>* twy;
+  const T* ktab;     // kx values (half entries), then ky values (ny entries)
+  const T* gtab;     // Gaussian factors, same layout
+  int rb1, rb2;      // rows per item for one- and two-field row passes
+  unsigned nblocks;
+
+  __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH), sh(shr) {
+    nx = d.nx; ny = d.ny; lgx = d.lgx; lgy = d.lgy; half = nx / 2; nkx = half + 1;
+    nspec = (long long)nkx * ny;
+    ncell = (long long)nx * ny;
+    Sa = (C2<T>*)d.Sa; Sb = (C2<T>*)d.Sb;
+    hd = (T*)d.hd; u = (T*)d.u; q1 = (const T*)d.q1; q2 = (const T*)d.q2;
+    mask = d.mask; jcmap = (const T*)d.jcmap;
+    twx = (const C2<T>*)d.tw_x; twy = (const C2<T>*)d.tw_y;
+    ktab = (const T*)d.ktab;
+    gtab = (const T*)d.gtab;
+    rb1 = d.rows_per_item;
+    rb2 = d.zs_per_item;
+    nblocks = gridDim.x;
+  }
+
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
+
+  // ---- y pass: forward, multiplier, inverse on x-wavenumber line kx ----
+  __device__ void col_item(int kx, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
+    lines_load<T>(sm, Sin + (long long)kx * ny, nspec, nin, lgy);
+    C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nin, twy);
+    C2<T>* Y = X == sm ? sm2 : sm;
+    const T s = (T)1 / (T)ncell;
+    const T kxv = ktab[kx], gx = gtab[kx];
+    const T kxo = (kx == half) ? (T)0 : kxv;
+    for (int ky = threadIdx.x; ky < ny; ky += NT) {
+      const T kyv = ktab[nkx + ky], G = gx * gtab[nkx + ky];
+      const T kyo = (ky == ny / 2) ? (T)0 : kyv;
+      const T k2 = kxv * kxv + kyv * kyv;
+      C2<T> a = X[ky];
+      if (op == OP_GRAD) {
+        const T fx = kxo * G * s, fy = kyo * G * s;
+        X[ky] = cmul_si(cscale(a, fx), 1);
+        X[ny + ky] = cmul_si(cscale(a, fy), 1);
+      } else if (op == OP_CURLNEG) {
+        const C2<T> b = X[ny + ky];
+        // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
+        C2<T> c = {kyo * a.x - kxo * b.x, kyo * a.y - kxo * b.y};
+        X[ky] = cmul_si(cscale(c, G * s), 1);
+      } else {
+        T m;
+        const T kabs = sqrt(k2);
+        if (op == OP_K1) m = (k2 > (T)0) ? (T)2 / kabs : (T)0;
+        else if (op == OP_K2) m = (T)d.lam * kabs * (T)0.5 * G;
+        else if (op == OP_KH) m = kabs * (T)0.5;
+        else m = (T)1;
+        X[ky] = cscale(a, m * s);
+      }
+    }
+    __syncthreads();
+    const C2<T>* Z = fft_lines<T, +1>(X, Y, lgy, nout, twy);
+    lines_store<T>(Z, Sout + (long long)kx * ny, nspec, nout, lgy);
+  }
+
+  __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
+    for (int kx = blockIdx.x; kx < nkx; kx += nblocks) col_item(kx, Sin, nin, Sout, nout, op);
+  }
+
+  // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
+  // epi(row, x, in[], out[]) is called for every cell of the item.
+  template <int NIN, int NOUT, class Epi>
+  __device__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi) {
+    const int npair = rb / 2;
+    C2<T>* X = sm;
+    if (NIN > 0) X = rows_gather_inverse<T>(sm, sm2, Sin + y0, nspec, ny, NIN, npair, lgx, twx);
+    C2<T>* Y = X == sm ? sm2 : sm;
+    for (int e = threadIdx.x; e < (npair << lgx); e += NT) {
+      const int pr = e >> lgx, x = e & (nx - 1);
+      T ina[NIN > 0 ? NIN : 1], inb[NIN > 0 ? NIN : 1], oa[NOUT > 0 ? NOUT : 1], ob[NOUT > 0 ? NOUT : 1];
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) {
+        const C2<T> z = X[((f * npair + pr) << lgx) + x];
+        ina[f] = z.x; inb[f] = z.y;
+      }
+      epi(y0 + 2 * pr, x, ina, oa);
+      epi(y0 + 2 * pr + 1, x, inb, ob);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) X[((f * npair + pr) << lgx) + x] = C2<T>{oa[f], ob[f]};
+    }
+    __syncthreads();
+    if (NOUT > 0) rows_forward_scatter<T>(X, Y, Sout + y0, nspec, ny, NOUT, npair, lgx, twx);
+  }
+
+  // rows pass with an optional per-item reduction into partials slot `slot`
+  template <int NIN, int NOUT, class Epi>
+  __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
+    const int nitems = ny / rb;
+    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+      epi.acc = 0.0;
+      epi.accmax = 0.0;
+      row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
+      if (slot >= 0) {
+        const double v = epi.is_max ? block_max(epi.accmax, sh.red) : block_sum(epi.acc, sh.red);
+        if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
+      }
+    }
+  }
+  __device__ double total(int slot, int rb, bool is_max = false) {
+    return reduce_partials(d.partials, d.max_items, slot, ny / rb, is_max, sh.red);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// applied field
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int he_segment(const Desc& d, double t) {
+  if (d.he_knots <= 0) return 0;
+  int k = -1;
+  for (int i = 0; i < d.he_knots; ++i)
+    if (d.he_t[i] <= t) k = i;
+  return k;
+}
+__device__ __forceinline__ double he_value(const Desc& d, double t) {
+  if (d.he_knots <= 0) return d.he_sin_amp * sin(2.0 * PI_D * t / d.he_sin_period);
+  const int k = he_segment(d, t);
+  if (k < 0) return d.he_v[0];
+  if (k >= d.he_knots - 1) return d.he_v[d.he_knots - 1];
+  const double s = (t - d.he_t[k]) / (d.he_t[k + 1] - d.he_t[k]);
+  return d.he_v[k] + s * (d.he_v[k + 1] - d.he_v[k]);
+}
+__device__ __forceinline__ double he_dot(const Desc& d, double t, int seg) {
+  if (d.he_knots <= 0) {
+    const double w = 2.0 * PI_D / d.he_sin_period;
+    return d.he_sin_amp * w * cos(w * t);
+  }
+  const int k = (seg == -2) ? he_segment(d, t) : seg;
+  if (k < 0 || k >= d.he_knots - 1) return 0.0;
+  return (d.he_v[k + 1] - d.he_v[k]) / (d.he_t[k + 1] - d.he_t[k]);
+}
+__device__ __forceinline__ double he_next_knot(const Desc& d, double t) {
+  for (int i = 0; i < d.he_knots; ++i)
+    if (d.he_t[i] > t) return d.he_t[i];
+  return INFINITY;
+}
+
+// ------------------------------------------------------------------------------------------
+// epilogues
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct EpiBase {
+  double acc = 0.0, accmax = 0.0;
+  bool is_max = false;
+};
+
+// P1 / readouts: field from the FP64 stage input
+template <typename T>
+struct EpiStage : EpiBase<T> {
+  const Film<T>* F;
+  StageIn in;
+  __device__ void operator()(int y, int x, const T*, T* out) {
+    const long long i = (long long)y * F->nx + x;
+    double v = in.y[i];
+    for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][i];
+    if (in.ynew) in.ynew[i] = v;
+    this->acc += v;
+    out[0] = (T)v;
+  }
+};
+
+// mask indicator of free space (set-up of q1, q2)
+template <typename T>
+struct EpiOut : EpiBase<T> {
+  const Film<T>* F;
+  __device__ void operator()(int y, int x, const T*, T* out) {
+    out[0] = F->mask[(long long)y * F->nx + x] == 0 ? (T)1 : (T)0;
+  }
+};
+
+// store a real field (set-up, readouts)
+template <typename T>
+struct EpiStoreT : EpiBase<T> {
+  const Film<T>* F;
+  T* dst;
+  __device__ void operator()(int y, int x, const T* in, T*) {
+    dst[(long long)y * F->nx + x] = in[0];
+  }
+};
+template <typename T>
+struct EpiStoreHz : EpiBase<T> {
+  const Film<T>* F;
+  double* dst;
+  double he;
+  __device__ void operator()(int y, int x, const T* in, T*) {
+    dst[(long long)y * F->nx + x] = he + (double)in[0];
+  }
+};
+
+// P3: power law
+template <typename T>
+struct EpiPower : EpiBase<T> {
+  const Film<T>* F;
+  T n, e0, jc, rho_out;
+  __device__ void operator()(int y, int x, const T* in, T* out) {
+    const long long i = (long long)y * F->nx + x;
+    const T gx = in[0], gy = in[1];
+    const T jx = gy, jy = -gx;                              // Eq. 2
+    const int m = F->mask[i];
+    const T jcl = F->jcmap ? F->jcmap[i] : jc;
+    const T rho = resistivity<T>(jx * jx + jy * jy, jcl, m, n, e0, rho_out);
+    out[0] = rho * jx;                                      // Eq. 3
+    out[1] = rho * jy;
+  }
+};
+
+// P5: initial h_dot (warm start), sum over D
+template <typename T>
+struct EpiInit : EpiBase<T> {
+  const Film<T>* F;
+  bool warm;
+  T A_prev, hed;
+  __device__ void operator()(int y, int x, const T* in, T* out) {
+    const long long i = (long long)y * F->nx + x;
+    const int m = F->mask[i];
+    T h;
+    if (m != 0) h = in[0];                                  // h_dot_in on the conductor
+    else h = warm ? F->hd[i] - A_prev : hed;                // warm start (Section 2.2)
+    F->hd[i] = h;
+    this->acc += (double)h;
+    out[0] = h;
+  }
+};
+
+// P7: u = raw - A q1; sum over free space; forward of mask_out u
+template <typename T>
+struct EpiU : EpiBase<T> {
+  const Film<T>* F;
+  T A;
+  __device__ void operator()(int y, int x, const T* in, T* out) {
+    const long long i = (long long)y * F->nx + x;
+    const T v = in[0] - A * F->q1[i];
+    F->u[i] = v;
+    const bool o = F->mask[i] == 0;
+    if (o) this->acc += (double)v;
+    out[0] = o ? v : (T)0;
+  }
+};
+
+// P8: residual sum over free space of |u - C|
+template <typename T>
+struct EpiResid : EpiBase<T> {
+  const Film<T>* F;
+  double C;
+  __device__ void operator()(int y, int x, const T*, T*) {
+    const long long i = (long long)y * F->nx + x;
+    if (F->mask[i] == 0) this->acc += fabs((double)F->u[i] - C);
+  }
+};
+
+// P10: h_dot update on free space (Eq. 12), sum over D, forward
+template <typename T>
+struct EpiUpdate : EpiBase<T> {
+  const Film<T>* F;
+  T A, C;
+  __device__ void operator()(int y, int x, const T* in, T* out) {
+    const long long i = (long long)y * F->nx + x;
+    T h = F->hd[i];
+    if (F->mask[i] == 0) {
+      const T w = in[0] - C * F->q2[i];
+      h = (h - A) - w;
+      F->hd[i] = h;
+    }
+    this->acc += (double)h;
+    out[0] = h;
+  }
+};
+
+// finalize: g_dot = (u - C) on the conductor; optional BS23 error contribution
+template <typename T>
+struct EpiFinal : EpiBase<T> {
+  const Film<T>* F;
+  double C;
+  double* kout;
+  // error estimate (stage 4 of a step): E = h (e1 k1 + e2 k2 + e3 k3 + e4 k4)
+  bool err;
+  double h, rtol, atol;
+  const double* k1; const double* k2; const double* k3; const double* y; const double* ynew;
+  __device__ void operator()(int yy, int x, const T*, T*) {
+    const long long i = (long long)yy * F->nx + x;
+    const double g = F->mask[i] != 0 ? (double)F->u[i] - C : 0.0;
+    kout[i] = g;
+    if (err) {
+      const double E = h * (-5.0 / 72.0 * k1[i] + 1.0 / 12.0 * k2[i] + 1.0 / 9.0 * k3[i] - 0.125 * g);
+      const double sc = atol + rtol * fmax(fabs(y[i]), fabs(ynew[i]));
+      double q = fabs(E) / sc;
+      if (!(q == q) || isinf(q)) q = 1e300;                  // non-finite -> rejected step
+      this->accmax = fmax(this->accmax, q);
+    } else {
+      if (!isfinite(g)) this->accmax = 1.0;
+    }
+  }
+};
+
+// magnetization: sum over D of g (times dx dy on the host side)
+template <typename T>
+struct EpiMoment : EpiBase<T> {
+  const Film<T>* F;
+  const double* g;
+  __device__ void operator()(int y, int x, const T*, T*) {
+    this->acc += g[(long long)y * F->nx + x];
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// one right-hand side.  Returns ST_OK / ST_NOCONV / ST_BARRIER (same in every CTA).
+// ------------------------------------------------------------------------------------------
+struct RhsOut {
+  int status, iters;
+  double r;
+  double err;          // BS23 error norm when requested
+  int nonfinite;
+};
+
+template <typename T>
+__device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const StageIn& sin, double* kout,
+                           int force_iters, bool want_err, double h_err, const double* e_k1,
+                           const double* e_k2, const double* e_k3, const double* e_y,
+                           const double* e_ynew) {
+  const Desc& d = F.d;
+  RhsOut res{ST_OK, 0, 0.0, 0.0, 0};
+  const double hed = he_dot(d, t, seg);
+  const double N = (double)F.ncell;
+  const double nout = (double)d.nout;
+
+  // P1
+  {
+    EpiStage<T> e; e.F = &F; e.in = sin;
+    F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, -1);
+  }
+  if (!F.sync(1)) { res.status = ST_BARRIER; return res; }
+  F.cols(F.Sa, 1, F.Sa, 2, OP_GRAD);                                    // P2
+  if (!F.sync(2)) { res.status = ST_BARRIER; return res; }
+  {
+    EpiPower<T> e; e.F = &F;
+    e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+    F.rows<2, 2>(F.rb2, F.Sa, F.Sb, e, -1);                             // P3
+  }
+  if (!F.sync(3)) { res.status = ST_BARRIER; return res; }
+  F.cols(F.Sb, 2, F.Sb, 1, OP_CURLNEG);                                 // P4
+  if (!F.sync(4)) { res.status = ST_BARRIER; return res; }
+
+  const bool have_out = d.nout > 0;
+  {
+    EpiInit<T> e; e.F = &F;
+    e.warm = F.sh.warm_valid != 0; e.A_prev = (T)F.sh.A_prev; e.hed = (T)hed;
+    F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                              // P5
+  }
+  if (!F.sync(5)) { res.status = ST_BARRIER; return res; }
+  double A = have_out ? (F.total(0, F.rb1) - N * hed) / nout : 0.0;    // Eq. 10
+  double C = 0.0, r = 0.0;
+  const bool forced = force_iters > 0;
+  const bool fixed = d.iter_tol <= 0.0;
+  int itmax = forced ? force_iters : d.iter_max;
+  if (!have_out) itmax = 1;
+  int i = 0;
+  for (; i < itmax; ++i) {
+    F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                    // P6
+    if (!F.sync(6)) { res.status = ST_BARRIER; return res; }
+    {
+      EpiU<T> e; e.F = &F; e.A = (T)A;
+      F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 1);                            // P7
+    }
+    if (!F.sync(7)) { res.status = ST_BARRIER; return res; }
+    if (!have_out) { C = 0.0; r = 0.0; break; }
+    C = F.total(1, F.rb1) / nout;                                       // Eq. 11
+    {
+      EpiResid<T> e; e.F = &F; e.C = C;
+      F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 2);                       // P8
+    }
+    if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
+    r = F.total(2, F.rb1) / nout;
+    const bool last = (i == itmax - 1);
+    const bool stop = (forced || fixed) ? last : (r < d.iter_tol || last);
+    if (stop) break;
+    F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                    // P9
+    if (!F.sync(9)) { res.status = ST_BARRIER; return res; }
+    {
+      EpiUpdate<T> e; e.F = &F; e.A = (T)A; e.C = (T)C;
+      F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                            // P10
+    }
+    if (!F.sync(10)) { res.status = ST_BARRIER; return res; }
+    A = (F.total(0, F.rb1) - N * hed) / nout;                           // Eq. 10
+  }
+  res.iters = i + 1;
+  res.r = r;
+  res.status = (!have_out || fixed || r < d.iter_tol) ? ST_OK : ST_NOCONV;
+  // warm start for the next call: h_dot stored, A still to subtract on free space
+  F.sh.warm_valid = 1;
+  F.sh.A_prev = A;
+
+  // finalize
+  {
+    EpiFinal<T> e; e.F = &F; e.C = C; e.kout = kout; e.is_max = true;
+    e.err = want_err; e.h = h_err; e.rtol = d.rtol; e.atol = d.atol;
+    e.k1 = e_k1; e.k2 = e_k2; e.k3 = e_k3; e.y = e_y; e.ynew = e_ynew;
+    F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 3);
+  }
+  if (!F.sync(11)) { res.status = ST_BARRIER; return res; }
+  const double q = F.total(3, F.rb1, true);
+  if (want_err) res.err = q;
+  else res.nonfinite = q > 0.0;
+  return res;
+}
+
+// ------------------------------------------------------------------------------------------
+// the persistent kernel
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT, 1) film_kernel(Desc d, KernelArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sm = (C2<T>*)smraw;
+  __shared__ Shared sh;
+  SolverState* st = d.st;
+  if (threadIdx.x == 0) {
+    sh.warm_valid = st->warm_valid;
+    sh.A_prev = st->A_prev;
+  }
+  __syncthreads();
+  Film<T> F(d, sm, sh);
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int status = ST_OK;
+
+  if (a.mode == MODE_SETUP) {
+    // q1 = F^-1[K1 F(out)], q2 = F^-1[K2 F(out)]
+    for (int pass = 0; pass < 2; ++pass) {
+      EpiOut<T> eo; eo.F = &F;
+      F.rows<0, 1>(F.rb1, nullptr, F.Sa, eo, -1);
+      if (!F.sync(20)) { status = ST_BARRIER; break; }
+      F.cols(F.Sa, 1, F.Sa, 1, pass == 0 ? OP_K1 : OP_K2);
+      if (!F.sync(21)) { status = ST_BARRIER; break; }
+      EpiStoreT<T> es; es.F = &F; es.dst = (T*)(pass == 0 ? d.q1 : d.q2);
+      F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
+      if (!F.sync(22)) { status = ST_BARRIER; break; }
+    }
+  } else if (a.mode == MODE_HZ) {
+    EpiStage<T> e; e.F = &F; e.in = StageIn{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, -1);
+    if (F.sync(30)) {
+      F.cols(F.Sa, 1, F.Sa, 1, OP_KH);
+      if (F.sync(31)) {
+        EpiStoreHz<T> es; es.F = &F; es.dst = a.out; es.he = he_value(d, a.t);
+        F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
+      } else status = ST_BARRIER;
+    } else status = ST_BARRIER;
+  } else if (a.mode == MODE_MOMENT) {
+    EpiMoment<T> e; e.F = &F; e.g = a.y_in;
+    F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 4);
+    if (F.sync(40)) {
+      const double s = F.total(4, F.rb1);
+      if (leader) a.out[0] = s * d.dx * d.dy;
+    } else status = ST_BARRIER;
+  } else if (a.mode == MODE_RHS) {
+    StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    RhsOut r = film_rhs<T>(F, a.t, a.seg, in, a.out, a.force_iters, false, 0.0, nullptr, nullptr,
+                           nullptr, nullptr, nullptr);
+    status = r.status == ST_OK && r.nonfinite ? ST_NONFINITE : r.status;
+    if (leader) { st->last_iters = r.iters; st->last_r = r.r; st->n_rhs += 1; st->n_iters += r.iters; }
+  } else if (a.mode == MODE_ADVANCE) {
+    // BS23 with first-same-as-last, all decisions on the device
+    double t = st->t, h = st->h;
+    int failed = st->failed, k1_valid = st->k1_valid;
+    int iy = st->ybuf, iyn = st->ynewbuf, ik1 = st->k1buf, ik4 = st->k4buf;
+    // k2, k3 live in the two remaining buffers
+    int others[2], no = 0;
+    for (int b = 0; b < 6 && no < 2; ++b)
+      if (b != iy && b != iyn && b != ik1 && b != ik4) others[no++] = b;
+    const int ik2 = others[0], ik3 = others[1];
+    long long att = 0, n_rhs = 0, n_it = 0, n_acc = 0, n_rej = 0, n_nc = 0;
+    double last_r = 0.0, last_err = 0.0;
+    while (t < a.t_target && att < a.max_attempts) {
+      const double t_lim = fmin(a.t_target, he_next_knot(d, t));
+      const bool clipped = t + 1.1 * h >= t_lim;
+      if (clipped) h = t_lim - t;
+      const int seg = he_segment(d, t);
+      int it[4] = {-1, -1, -1, -1};
+      double* y = d.fbuf[iy];
+      double* yn = d.fbuf[iyn];
+      double* k1 = d.fbuf[ik1];
+      double* k2 = d.fbuf[ik2];
+      double* k3 = d.fbuf[ik3];
+      double* k4 = d.fbuf[ik4];
+      RhsOut r;
+      if (!k1_valid) {
+        StageIn in{y, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+        r = film_rhs<T>(F, t, seg, in, k1, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+        ++n_rhs; n_it += r.iters; it[0] = r.iters;
+        if (r.status != ST_OK) { status = r.status == ST_BARRIER ? ST_BARRIER : ST_NOCONV; break; }
+        if (r.nonfinite) { status = ST_NONFINITE; break; }
+        k1_valid = 1;
+      }
+      int outcome = 1;
+      double err = INFINITY;
+      StageIn s2{y, 1, {0.5 * h, 0, 0}, {k1, nullptr, nullptr}, nullptr};
+      r = film_rhs<T>(F, t + 0.5 * h, seg, s2, k2, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+      ++n_rhs; n_it += r.iters; it[1] = r.iters;
+      if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+      if (r.status == ST_OK) {
+        StageIn s3{y, 1, {0.75 * h, 0, 0}, {k2, nullptr, nullptr}, nullptr};
+        r = film_rhs<T>(F, t + 0.75 * h, seg, s3, k3, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+        ++n_rhs; n_it += r.iters; it[2] = r.iters;
+        if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+      }
+      const double t_new = clipped ? t_lim : t + h;
+      if (r.status == ST_OK) {
+        StageIn s4{y, 3, {h * (2.0 / 9.0), h * (1.0 / 3.0), h * (4.0 / 9.0)}, {k1, k2, k3}, yn};
+        r = film_rhs<T>(F, t_new, seg, s4, k4, 0, true, h, k1, k2, k3, y, yn);
+        ++n_rhs; n_it += r.iters; it[3] = r.iters;
+        if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+        if (r.status == ST_OK) err = r.err;
+      }
+      last_r = r.r;
+      if (r.status != ST_OK) { outcome = 2; ++n_nc; }
+      else outcome = err <= 1.0 ? 1 : 0;
+      if (leader && st->log_count < d.log_cap) {
+        StepLog L; L.t = t; L.h = h; L.t_new = outcome == 1 ? t_new : t; L.err = err;
+        L.outcome = outcome; for (int q = 0; q < 4; ++q) L.iters[q] = it[q]; L.pad = 0;
+        d.log[st->log_count] = L;
+      }
+      if (leader) st->log_count += 1;
+      ++att;
+      if (outcome == 1) {
+        const bool knot_hit = clipped && t_lim == he_next_knot(d, t);
+        t = t_new;
+        int tmp = iy; iy = iyn; iyn = tmp;
+        tmp = ik1; ik1 = ik4; ik4 = tmp;
+        k1_valid = knot_hit ? 0 : 1;
+        double fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -1.0 / 3.0)));
+        if (failed) fac = fmin(fac, 1.0);
+        h = h * fac;
+        failed = 0;
+        ++n_acc;
+        last_err = err;
+      } else if (outcome == 0) {
+        h = h * fmax(0.2, 0.9 * pow(err, -1.0 / 3.0));
+        failed = 1;
+        ++n_rej;
+      } else {
+        h = 0.5 * h;
+        failed = 1;
+        ++n_rej;
+      }
+      if (h < d.h_min) { status = ST_UNDERFLOW; break; }
+    }
+    if (leader) {
+      st->t = t; st->h = h; st->failed = failed; st->k1_valid = k1_valid;
+      st->ybuf = iy; st->ynewbuf = iyn; st->k1buf = ik1; st->k4buf = ik4;
+      st->n_attempts += att; st->n_rhs += n_rhs; st->n_iters += n_it; st->n_accepted += n_acc;
+      st->n_rejected += n_rej; st->n_noconv += n_nc; st->last_r = last_r; st->last_err = last_err;
+    }
+  }
+  if (leader) {
+    st->warm_valid = sh.warm_valid;
+    st->A_prev = sh.A_prev;
+    st->status = status;
+  }
+}
+
+size_t kernel_smem_bytes(int precision) {
+  return (size_t)2 * BATCH * (precision ? sizeof(C2<float>) : sizeof(C2<double>));
+}
+
+int film_max_blocks(int precision, size_t smem) {
+  int nb = 0;
+  if (precision) {
+    cudaFuncSetAttribute(film_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, film_kernel<float>, NT, smem);
+  } else {
+    cudaFuncSetAttribute(film_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, film_kernel<double>, NT, smem);
+  }
+  return nb;
+}
+
+cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s) {
+  Desc dd = d;
+  KernelArgs aa = a;
+  void* args[] = {&dd, &aa};
+  const size_t smem = kernel_smem_bytes(precision);
+  const void* fn = precision ? (const void*)film_kernel<float> : (const void*)film_kernel<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);
+}
+
+}  // namespace mf

@@ -1,0 +1,272 @@
+"""ctypes binding of the C interface in include/mf.h (argument marshalling only).
+
+Every computation runs in the CUDA library libmf.so; this module converts Python and torch
+arguments to plain pointers and sizes.  PyTorch provides the device memory (the workspace and
+state tensors) and the current CUDA stream.  Importing the module does not load the library;
+the first call does, and fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmf.so")
+
+MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_NOCONV, MF_ERR_NONFINITE = 0, 1, 2, 3, 4
+MF_ERR_STEP_UNDERFLOW, MF_ERR_WORKSPACE, MF_ERR_BARRIER = 5, 6, 7
+MF_READ_HZ, MF_READ_MOMENT, MF_READ_J = 0, 1, 2
+STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_NOCONV",
+                4: "MF_ERR_NONFINITE", 5: "MF_ERR_STEP_UNDERFLOW", 6: "MF_ERR_WORKSPACE",
+                7: "MF_ERR_BARRIER"}
+
+# every entry point declared in include/mf.h
+EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf_rhs_ex",
+           "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
+           "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
+           "mf_last_error", "mf_destroy"]
+
+
+class mf_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+        ("mask", ctypes.POINTER(ctypes.c_uint8)), ("jc_map", ctypes.POINTER(ctypes.c_double)),
+        ("jc", ctypes.c_double), ("n", ctypes.c_double), ("e0", ctypes.c_double),
+        ("rho_out", ctypes.c_double), ("sigma", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("iter_tol", ctypes.c_double), ("iter_max", ctypes.c_int), ("precision", ctypes.c_int),
+        ("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h0", ctypes.c_double),
+        ("h_min", ctypes.c_double),
+        ("he_t", ctypes.POINTER(ctypes.c_double)), ("he_v", ctypes.POINTER(ctypes.c_double)),
+        ("he_knots", ctypes.c_int), ("he_sin_amp", ctypes.c_double),
+        ("he_sin_period", ctypes.c_double), ("he_dir", ctypes.c_double * 3),
+    ]
+
+
+class mf_step_log(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("h", ctypes.c_double), ("t_new", ctypes.c_double),
+                ("err", ctypes.c_double), ("outcome", ctypes.c_int),
+                ("iters", ctypes.c_int * 4), ("pad", ctypes.c_int)]
+
+
+class mf_info(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("h", ctypes.c_double),
+                ("n_attempts", ctypes.c_longlong), ("n_accepted", ctypes.c_longlong),
+                ("n_rejected", ctypes.c_longlong), ("n_rhs", ctypes.c_longlong),
+                ("n_iters", ctypes.c_longlong), ("n_noconv", ctypes.c_longlong),
+                ("log_count", ctypes.c_longlong), ("last_iters", ctypes.c_int),
+                ("last_r", ctypes.c_double), ("last_err", ctypes.c_double),
+                ("grid", ctypes.c_int), ("threads", ctypes.c_int), ("smem_bytes", ctypes.c_int),
+                ("rows_per_item", ctypes.c_int), ("workspace_used", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libmf.so (built by paper_1801_04869_gb300/build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_1801_04869_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, dp, ip = ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_int)
+    sig = {
+        "mf_default_params": (None, [P(mf_params)]),
+        "mf_workspace_bytes": (ctypes.c_size_t, [P(mf_params)]),
+        "mf_create": (ctypes.c_int, [P(mf_params), vp, ctypes.c_size_t, vp, P(vp)]),
+        "mf_rhs": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, ip]),
+        "mf_rhs_ex": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, vp, vp, ctypes.c_int, ip]),
+        "mf_reset_warm": (ctypes.c_int, [vp]),
+        "mf_set_state": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, vp]),
+        "mf_get_state": (ctypes.c_int, [vp, dp, dp, vp]),
+        "mf_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_longlong]),
+        "mf_step": (ctypes.c_int, [vp, ctypes.c_double, ip]),
+        "mf_run_ramp": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, vp]),
+        "mf_readout": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+        "mf_readout_of": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, vp, vp]),
+        "mf_get_info": (ctypes.c_int, [vp, P(mf_info)]),
+        "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
+        "mf_last_error": (ctypes.c_char_p, [vp]),
+        "mf_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _arr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Problem:
+    """A problem set up in a torch-allocated device workspace (see mf_create in mf.h)."""
+
+    def __init__(self, *, dim: int, nx: int, ny: int, nz: int = 1, Lx: float, Ly: float,
+                 Lz: float = 0.0, mask, n: float, rho_out: float, precision: int = 0,
+                 jc: float = 1.0, jc_map=None, e0: float = 1.0, sigma: float = 0.0,
+                 lam: float = 0.7, iter_tol: float = 2e-4, iter_max: int = 1000,
+                 rtol: float = 1e-6, atol: float = 1e-6, h0: float = 0.0, h_min: float = 1e-12,
+                 he_knots=None, he_sin=None, he_dir=(0.0, 0.0, 1.0), device=None, stream=None):
+        import torch
+        lib = load()
+        self.lib = lib
+        p = mf_params()
+        lib.mf_default_params(ctypes.byref(p))
+        self._keep = []
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        self._keep.append(m)
+        p.dim, p.nx, p.ny, p.nz = dim, nx, ny, (1 if dim == 2 else nz)
+        p.Lx, p.Ly, p.Lz = Lx, Ly, Lz
+        p.mask = _arr(m, ctypes.c_uint8)
+        if jc_map is not None:
+            jm = np.ascontiguousarray(jc_map, dtype=np.float64).reshape(-1)
+            self._keep.append(jm)
+            p.jc_map = _arr(jm, ctypes.c_double)
+        p.jc, p.n, p.e0, p.rho_out, p.sigma = jc, n, e0, rho_out, sigma
+        p.lambda_, p.iter_tol, p.iter_max, p.precision = lam, iter_tol, iter_max, precision
+        p.rtol, p.atol, p.h0, p.h_min = rtol, atol, h0, h_min
+        if he_knots is not None:
+            kt = np.ascontiguousarray(he_knots[0], dtype=np.float64)
+            kv = np.ascontiguousarray(he_knots[1], dtype=np.float64)
+            self._keep += [kt, kv]
+            p.he_t, p.he_v, p.he_knots = _arr(kt, ctypes.c_double), _arr(kv, ctypes.c_double), len(kt)
+        else:
+            amp, per = he_sin if he_sin is not None else (0.0, 1.0)
+            p.he_knots, p.he_sin_amp, p.he_sin_period = 0, amp, per
+        p.he_dir[0], p.he_dir[1], p.he_dir[2] = he_dir
+        self.params = p
+        nbytes = lib.mf_workspace_bytes(ctypes.byref(p))
+        if nbytes == 0:
+            raise MFError(MF_ERR_ARG, "invalid parameters (mf_workspace_bytes returned 0)")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = lib.mf_create(ctypes.byref(p), ctypes.c_void_p(base + off), ctypes.c_size_t(nbytes),
+                           ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != MF_OK:
+            raise MFError(st, "mf_create failed")
+        self.h = h
+        self.dim, self.nx, self.ny, self.nz = dim, nx, ny, p.nz
+        self.state_len = nx * ny * (1 if dim == 2 else 3 * p.nz)
+
+    # -- helpers -----------------------------------------------------------------------------
+    def _check(self, st: int, allow=()):
+        if st != MF_OK and st not in allow:
+            raise MFError(st, self.lib.mf_last_error(self.h).decode())
+        return st
+
+    def state_tensor(self):
+        import torch
+        shape = (self.ny, self.nx) if self.dim == 2 else (3, self.nz, self.ny, self.nx)
+        return torch.zeros(shape, dtype=torch.float64, device=self.device)
+
+    # -- the C entry points ------------------------------------------------------------------
+    def mf_rhs(self, t: float, y, ydot, force_iters: int = 0, seg: int = -2, allow_noconv=False):
+        it = ctypes.c_int(0)
+        st = self.lib.mf_rhs_ex(self.h, t, seg, _dptr(y), _dptr(ydot), force_iters, ctypes.byref(it))
+        self._check(st, allow=(MF_ERR_NOCONV,) if allow_noconv else ())
+        return it.value, st
+
+    def mf_reset_warm(self):
+        self._check(self.lib.mf_reset_warm(self.h))
+
+    def mf_set_state(self, t: float, y=None, h: float = 0.0):
+        self._check(self.lib.mf_set_state(self.h, t, h, _dptr(y)))
+
+    def mf_get_state(self, y=None):
+        t, h = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.mf_get_state(self.h, ctypes.byref(t), ctypes.byref(h), _dptr(y)))
+        return t.value, h.value
+
+    def mf_advance(self, t_target: float, max_attempts: int = 1 << 40):
+        return self._check(self.lib.mf_advance(self.h, t_target, max_attempts))
+
+    def mf_step(self, t_max: float) -> bool:
+        acc = ctypes.c_int(0)
+        self._check(self.lib.mf_step(self.h, t_max, ctypes.byref(acc)))
+        return bool(acc.value)
+
+    def mf_run_ramp(self, t_out, want_fields: bool = False):
+        import torch
+        t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+        nm = 1 if self.dim == 2 else 3
+        m = np.zeros(len(t_out) * nm)
+        fields = None
+        if want_fields:
+            per = self.nx * self.ny if self.dim == 2 else 3 * self.nx * self.ny * self.nz
+            fields = torch.zeros((len(t_out), per), dtype=torch.float64, device=self.device)
+        self._check(self.lib.mf_run_ramp(self.h, len(t_out), _arr(t_out, ctypes.c_double),
+                                         _arr(m, ctypes.c_double), _dptr(fields)))
+        return m.reshape(len(t_out), nm), fields
+
+    def mf_readout(self, what: int, out=None, t=None, y=None):
+        if what == MF_READ_MOMENT:
+            nm = 1 if self.dim == 2 else 3
+            host = np.zeros(nm)
+            ptr = ctypes.c_void_p(host.ctypes.data)
+            if y is None:
+                self._check(self.lib.mf_readout(self.h, what, ptr))
+            else:
+                self._check(self.lib.mf_readout_of(self.h, what, t, _dptr(y), ptr))
+            return host
+        if y is None:
+            self._check(self.lib.mf_readout(self.h, what, _dptr(out)))
+        else:
+            self._check(self.lib.mf_readout_of(self.h, what, t, _dptr(y), _dptr(out)))
+        return out
+
+    def mf_get_info(self) -> dict:
+        inf = mf_info()
+        self._check(self.lib.mf_get_info(self.h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in mf_info._fields_}
+
+    def mf_get_log(self, cap: int = 1 << 16):
+        buf = (mf_step_log * cap)()
+        cnt = ctypes.c_longlong(0)
+        self._check(self.lib.mf_get_log(self.h, buf, cap, ctypes.byref(cnt)))
+        n = min(cnt.value, cap)
+        return [(e.t, e.h, e.t_new, e.outcome, tuple(e.iters), e.err) for e in buf[:n]]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_workload(wl, **over) -> Problem:
+    """Problem for a workloads.Workload description."""
+    kw = dict(dim=wl.dim, nx=wl.nx, ny=wl.ny, nz=wl.nz, Lx=wl.Lx, Ly=wl.Ly, Lz=wl.Lz,
+              mask=wl.mask, n=wl.n, rho_out=wl.rho_out, precision=wl.precision,
+              jc=wl.jc, jc_map=wl.jc_map, sigma=wl.sigma, lam=wl.lam, iter_tol=wl.iter_tol,
+              iter_max=wl.iter_max, rtol=wl.rtol, atol=wl.atol, he_knots=wl.he_knots,
+              he_sin=wl.he_sin, he_dir=wl.vector_he)
+    kw.update(over)
+    return Problem(**kw)

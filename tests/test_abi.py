@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/mf.h
+(no GPU needed: nothing is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mf_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_04869_gb300 import build, native
+    if not os.path.exists(native.LIB_PATH):
+        build.build()
+    return native.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1801_04869_gb300 import native
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(native.EXPORTS) | {"mf_default_params"}
+
+
+def test_struct_layouts_match_header(lib):
+    from paper_1801_04869_gb300 import native
+    p = native.mf_params()
+    lib.mf_default_params(ctypes.byref(p))
+    assert p.n == 19.0 and p.lambda_ == 0.7 and p.iter_tol == 2e-4 and p.he_dir[2] == 1.0
+
+
+def test_workspace_query_and_argument_checks(lib):
+    import numpy as np
+    from paper_1801_04869_gb300 import native
+    p = native.mf_params()
+    lib.mf_default_params(ctypes.byref(p))
+    m = np.zeros(128 * 128, np.uint8)
+    p.nx = p.ny = 128
+    p.Lx = p.Ly = 2.0
+    p.mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    p.he_sin_period = 1.0
+    b = lib.mf_workspace_bytes(ctypes.byref(p))
+    assert b > 128 * 128 * 8 * 6
+    p.nx = 100                                    # not a power of two
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) == 0
+    p.nx = 4096                                   # beyond the film limit
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) == 0
+    h = ctypes.c_void_p()
+    p.nx = 128
+    assert lib.mf_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == native.MF_ERR_WORKSPACE

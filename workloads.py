@@ -172,7 +172,7 @@ class Workload:
     sigma: float = 0.0                              # <= 0: sqrt(sum dx^2)
     lam: float = 0.7
     iter_tol: float = 2e-4
-    iter_max: int = 100
+    iter_max: int = 3000          # a cold start (t = 0, g = 0) needs ~700 iterations at 128^2
     rtol: float = 1e-6
     atol: float = 1e-6
     jc: float = 1.0
