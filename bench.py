@@ -1,0 +1,328 @@
+"""Benchmark: right-hand-side evaluations per second of the FFT method-of-lines film solver.
+
+Workload: rectangular film 1024 x 512 cells (aspect 2:1) in a 2048 x 2048 periodic grid, n = 30,
+h_e = 0.8 sin(2 pi t), FP32 transforms and power law with FP64 state (precision form).  One
+benchmark step is one BS23 step attempt of the whole right-hand-side path (stage input,
+smoothed gradient, power law, curl, warm-started outside iteration with its stop test, error
+norm and step control), all in the persistent CUDA kernel.  The metric counts every
+right-hand-side evaluation the steps performed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torch.distributed.run): every rank advances its own replica of the film (the film
+does not shard); value = all ranks' evaluations / max time over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "RHS evals/s"
+UNIT = "RHS/s"
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1801_04869_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per algorithmic byte from the committed ncu capture of this kernel, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == src and parts[1] == kernel and parts[2] == workload:
+            return float(parts[3])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rhs_bytes(n_rhs: int, n_iters: int, M: float) -> float:
+    """Algorithmic HBM bytes of the film right-hand side: (19 + 14 I) M per evaluation,
+    M = bytes of one real field at transform precision, I = outside iterations."""
+    return (19.0 * n_rhs + 14.0 * n_iters) * M
+
+
+def _oracle_problem(wl):
+    from oracle.film2d import FilmProblem
+    from oracle.waveform import Waveform
+    wf = Waveform(*wl.he_knots) if wl.he_knots else Waveform(sin_amp=wl.he_sin[0], sin_period=wl.he_sin[1])
+    return FilmProblem(wl.nx, wl.ny, wl.Lx, wl.Ly, wl.mask, n=wl.n, rho_out=wl.rho_out, waveform=wf,
+                       iter_tol=wl.iter_tol, iter_max=wl.iter_max, lam=wl.lam)
+
+
+def cpu_sample(wl, iters: int, budget_s: float):
+    """Time forced-iteration oracle right-hand sides of the workload until `budget_s` is used."""
+    import workloads as W
+    o = _oracle_problem(wl)
+    g = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=3, amplitude=0.4)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.rhs(0.05 + 1e-4 * n, g, None, max(1, iters))
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    return n / el, n, el
+
+
+def cores_used() -> int:
+    # numpy's FFT (pocketfft) and elementwise kernels run on one thread
+    return 1
+
+
+def run_reference(args):
+    import workloads as W
+    wl = W.rect_film_2048(precision=1)
+    iters = 5
+    rate, n, el = cpu_sample(wl, iters, budget_s=max(5.0, 20.0 * args.steps / max(args.steps, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny], "n": wl.n,
+                       "iterations_per_rhs": iters},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{n} right-hand sides of the {wl.nx}x{wl.ny} film with "
+                                       f"{iters} forced outside iterations each"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1801_04869_gb300 import native
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = W.rect_film_2048(precision=1, n_grid=args.grid)
+    p = native.from_workload(wl)
+    stream = p.stream
+    ncell = wl.nx * wl.ny
+    M = ncell * 4.0                                     # one FP32 real field
+
+    # start mid-cycle from a seeded critical-state film so that the warm-up absorbs the cold
+    # start of the outside iteration
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100 + rank, amplitude=0.3)
+    y = torch.as_tensor(g0, device="cuda")
+    t_start = 0.05
+    p.mf_set_state(t_start, y, h=2e-5)
+    p.mf_advance(1.0, max_attempts=max(1, args.warmup))
+    torch.cuda.synchronize()
+
+    def counters():
+        i = p.mf_get_info()
+        return i["n_rhs"], i["n_iters"], i["n_attempts"]
+
+    r0, it0, a0 = counters()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as ck:
+        ev0.record(stream)
+        p.mf_advance(1.0, max_attempts=args.steps)     # one persistent launch, K step attempts
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    r1, it1, a1 = counters()
+    n_rhs, n_it, n_att = r1 - r0, it1 - it0, a1 - a0
+    # the integrator may stop early only at t = 1 (end of the cycle)
+    t_now, _ = p.mf_get_state()
+
+    # end-to-end through the public API with host buffers: H2D state, one step, D2H state + m_z
+    host = torch.empty((wl.ny, wl.nx), dtype=torch.float64).pin_memory()
+    dev_y = torch.empty((wl.ny, wl.nx), dtype=torch.float64, device="cuda")
+    p.mf_get_state(dev_y)
+    host.copy_(dev_y)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    re0, ie0, _ = counters()
+    t_e = t_now
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dev_y.copy_(host, non_blocking=True)
+        p.mf_set_state(t_e, dev_y)
+        p.mf_advance(1.0, max_attempts=1)
+        t_e, _ = p.mf_get_state(dev_y)
+        host.copy_(dev_y, non_blocking=True)
+        m = p.mf_readout(native.MF_READ_MOMENT)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    re1, ie1, _ = counters()
+    e2e_rate = (re1 - re0) / e2e_s
+
+    sec = ms / 1000.0
+    if dist:
+        tt = torch.tensor([sec, float(n_rhs)], device="cuda", dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        sec_all, rhs_all = float(mx[0]), float(tt[1])
+        e = torch.tensor([e2e_rate], device="cuda", dtype=torch.float64)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        e2e_all = float(e[0])
+    else:
+        sec_all, rhs_all, e2e_all = sec, float(n_rhs), e2e_rate
+
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        mean_it = n_it / max(n_rhs, 1)
+        alg = rhs_bytes(n_rhs, n_it, M)
+        achieved = alg / sec / 1e9
+        traffic_ratio = profiled_traffic("film_kernel_f32", wl.name)
+        cpu = None
+        if not args.no_cpu:
+            rate, n, el = cpu_sample(wl, max(1, round(mean_it)), budget_s=15.0)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                   "sample": f"{n} FP64 right-hand sides of the {wl.nx}x{wl.ny} film with "
+                             f"{max(1, round(mean_it))} forced outside iterations each "
+                             f"({el:.1f} s on the host)"}
+        info = p.mf_get_info()
+        line = {
+            "metric": METRIC, "value": rhs_all / sec_all, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny], "film_cells": [wl.nx // 2, wl.ny // 4],
+                       "n": wl.n, "he": "0.8 sin(2 pi t)", "state": "f64", "transforms": "f32",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set > L2 (no flush)", "t_start": t_start, "t_end": t_now,
+                       "step_attempts": n_att, "rhs_evals": n_rhs,
+                       "mean_outside_iterations": mean_it, "grid_ctas": info["grid"],
+                       "threads": info["threads"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": None if traffic_ratio is None else traffic_ratio * alg,
+                         "traffic_note": "ncu dram bytes of a 1-step launch, scaled to this launch by its algorithmic bytes",
+                         "kernel": "film_kernel<float> (persistent)",
+                         "bytes_model": "(19 + 14 I) M per RHS, M = 2048^2 x 4 B"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": ncell * 8,
+                    "d2h_bytes_per_step": ncell * 8 + 8},
+            "gpu_launches": 1,
+            "clocks": ck.summary(),
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

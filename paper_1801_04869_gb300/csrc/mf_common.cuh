@@ -12,6 +12,10 @@ namespace mf {
 constexpr int NT = 256;           // threads per CTA of the persistent kernels
 constexpr int VPT = 16;           // complex values each thread holds per FFT stage
 constexpr int BATCH = NT * VPT;   // complex points one CTA transforms at once (4096)
+// shared-memory position of FFT element e: one padding slot every 16 complex values keeps the
+// strided butterfly writes of the early Stockham stages to at most 2-way bank conflicts
+__host__ __device__ __forceinline__ constexpr int sp(int e) { return e + (e >> 4); }
+constexpr int BATCH_PAD = BATCH + BATCH / 16;
 
 // ------------------------------------------------------------------------------------------
 // complex numbers

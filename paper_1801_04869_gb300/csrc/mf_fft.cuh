@@ -2,7 +2,7 @@
 // radix-2 stage), the building block of every row, column and z pass.
 //
 // A CTA of NT threads transforms `nlines` lines of length L (a power of two, 2..4096) that
-// sit back to back in shared memory, nlines * L <= BATCH.  Stages alternate between two
+// sit back to back in shared memory (element e at position sp(e)), nlines * L <= BATCH.  Stages alternate between two
 // shared buffers (each thread keeps one butterfly in registers).  Twiddles come from a global table
 // tw[m] = exp(-2 pi i m / L) (read-only, cached); the inverse uses their conjugates and is
 // unnormalised.
@@ -64,10 +64,10 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, 
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int line = b >> lgq, i = b & (q - 1);
     const int k = i & (p - 1);
-    const C2<T>* src = in + (line << lgL) + i;
+    const int src = (line << lgL) + i;
     C2<T> v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = src[j << lgq];
+    for (int j = 0; j < R; ++j) v[j] = in[sp(src + (j << lgq))];
     if (lgp > 0) {
       // w^(j k) = tw[j k L / (p R)] (conjugated for DIR > 0)
       const int step = k << (lgL - lgp - LGR);
@@ -79,9 +79,9 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, 
       }
     }
     dft<T, R, DIR>(v);
-    C2<T>* dst = out + (line << lgL) + ((i - k) << LGR) + k;
+    const int dst = (line << lgL) + ((i - k) << LGR) + k;
 #pragma unroll
-    for (int j = 0; j < R; ++j) dst[j << lgp] = v[j];
+    for (int j = 0; j < R; ++j) out[sp(dst + (j << lgp))] = v[j];
   }
   __syncthreads();
 }

@@ -10,8 +10,8 @@
 //   loop (Eqs. 11-12):
 //   P6  y pass: 2/|k|
 //   P7  x pass: u = raw - A q1, sum over free space (C), forward of mask_out u
-//   P8  residual r = mean_out |u - C| (stop test, Section 2.3)
-//   P9  y pass: lambda (|k|/2) G
+//   P8  residual r = mean_out |u - C| (stop test, Section 2.3), in the same phase as
+//   P9  y pass: lambda (|k|/2) G (discarded when the stop test ends the loop)
 //   P10 x pass: h_dot_out <- h_dot_out - A - (w - C q2), sum for the next A, forward
 //   end: g_dot = (u - C) on the conductor, 0 on free space (FP64)
 // The constants A and C are applied through the precomputed fields q1 = F^-1[K1 F(out)] and
@@ -64,7 +64,7 @@ struct Film {
   int rb1, rb2;      // rows per item for one- and two-field row passes
   unsigned nblocks;
 
-  __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH), sh(shr) {
+  __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
     nx = d.nx; ny = d.ny; lgx = d.lgx; lgy = d.lgy; half = nx / 2; nkx = half + 1;
     nspec = (long long)nkx * ny;
     ncell = (long long)nx * ny;
@@ -93,16 +93,16 @@ struct Film {
       const T kyv = ktab[nkx + ky], G = gx * gtab[nkx + ky];
       const T kyo = (ky == ny / 2) ? (T)0 : kyv;
       const T k2 = kxv * kxv + kyv * kyv;
-      C2<T> a = X[ky];
+      C2<T> a = X[sp(ky)];
       if (op == OP_GRAD) {
         const T fx = kxo * G * s, fy = kyo * G * s;
-        X[ky] = cmul_si(cscale(a, fx), 1);
-        X[ny + ky] = cmul_si(cscale(a, fy), 1);
+        X[sp(ky)] = cmul_si(cscale(a, fx), 1);
+        X[sp(ny + ky)] = cmul_si(cscale(a, fy), 1);
       } else if (op == OP_CURLNEG) {
-        const C2<T> b = X[ny + ky];
+        const C2<T> b = X[sp(ny + ky)];
         // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
         C2<T> c = {kyo * a.x - kxo * b.x, kyo * a.y - kxo * b.y};
-        X[ky] = cmul_si(cscale(c, G * s), 1);
+        X[sp(ky)] = cmul_si(cscale(c, G * s), 1);
       } else {
         T m;
         const T kabs = sqrt(k2);
@@ -110,7 +110,7 @@ struct Film {
         else if (op == OP_K2) m = (T)d.lam * kabs * (T)0.5 * G;
         else if (op == OP_KH) m = kabs * (T)0.5;
         else m = (T)1;
-        X[ky] = cscale(a, m * s);
+        X[sp(ky)] = cscale(a, m * s);
       }
     }
     __syncthreads();
@@ -135,13 +135,13 @@ struct Film {
       T ina[NIN > 0 ? NIN : 1], inb[NIN > 0 ? NIN : 1], oa[NOUT > 0 ? NOUT : 1], ob[NOUT > 0 ? NOUT : 1];
 #pragma unroll
       for (int f = 0; f < NIN; ++f) {
-        const C2<T> z = X[((f * npair + pr) << lgx) + x];
+        const C2<T> z = X[sp(((f * npair + pr) << lgx) + x)];
         ina[f] = z.x; inb[f] = z.y;
       }
       epi(y0 + 2 * pr, x, ina, oa);
       epi(y0 + 2 * pr + 1, x, inb, ob);
 #pragma unroll
-      for (int f = 0; f < NOUT; ++f) X[((f * npair + pr) << lgx) + x] = C2<T>{oa[f], ob[f]};
+      for (int f = 0; f < NOUT; ++f) X[sp(((f * npair + pr) << lgx) + x)] = C2<T>{oa[f], ob[f]};
     }
     __syncthreads();
     if (NOUT > 0) rows_forward_scatter<T>(X, Y, Sout + y0, nspec, ny, NOUT, npair, lgx, twx);
@@ -432,13 +432,13 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
       EpiResid<T> e; e.F = &F; e.C = C;
       F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 2);                       // P8
     }
+    // P9 runs in the same phase as P8; its result is discarded when the test stops the loop
+    F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                    // P9
     if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
     r = F.total(2, F.rb1) / nout;
     const bool last = (i == itmax - 1);
     const bool stop = (forced || fixed) ? last : (r < d.iter_tol || last);
     if (stop) break;
-    F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                    // P9
-    if (!F.sync(9)) { res.status = ST_BARRIER; return res; }
     {
       EpiUpdate<T> e; e.F = &F; e.A = (T)A; e.C = (T)C;
       F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                            // P10
@@ -471,7 +471,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 // the persistent kernel
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NT, 1) film_kernel(Desc d, KernelArgs a) {
+__global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sm = (C2<T>*)smraw;
   __shared__ Shared sh;
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(NT, 1) film_kernel(Desc d, KernelArgs a) {
 }
 
 size_t kernel_smem_bytes(int precision) {
-  return (size_t)2 * BATCH * (precision ? sizeof(C2<float>) : sizeof(C2<double>));
+  return (size_t)2 * BATCH_PAD * (precision ? sizeof(C2<float>) : sizeof(C2<double>));
 }
 
 int film_max_blocks(int precision, size_t smem) {

@@ -30,12 +30,12 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
     const int pr = rest - k * npair;
     const C2<T>* p = src + f * fstride + (long long)k * kstride + 2 * pr;
     const C2<T> A = p[0], B = p[1];
-    C2<T>* Z = sm + ((f * npair + pr) << lgx);
+    const int z0 = (f * npair + pr) << lgx;
     if (k == 0 || k == half) {
-      Z[k] = C2<T>{A.x, B.x};
+      sm[sp(z0 + k)] = C2<T>{A.x, B.x};
     } else {
-      Z[k] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
-      Z[nx - k] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
+      sm[sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
+      sm[sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
     }
   }
   __syncthreads();
@@ -56,8 +56,8 @@ __device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C
     const int rest = e - f * per_f;
     const int k = rest / npair;
     const int pr = rest - k * npair;
-    const C2<T>* Z = sm + ((f * npair + pr) << lgx);
-    const C2<T> zk = Z[k], zm = Z[(nx - k) & (nx - 1)];
+    const int z0 = (f * npair + pr) << lgx;
+    const C2<T> zk = sm[sp(z0 + k)], zm = sm[sp(z0 + ((nx - k) & (nx - 1)))];
     const T hh = (T)0.5;
     C2<T> A = {hh * (zk.x + zm.x), hh * (zk.y - zm.y)};
     C2<T> B = {hh * (zk.y + zm.y), hh * (zm.x - zk.x)};   // -i (zk - conj(zm)) / 2
@@ -74,7 +74,7 @@ __device__ __forceinline__ void lines_load(C2<T>* sm, const C2<T>* src, long lon
   const int L = 1 << lgL;
   for (int e = threadIdx.x; e < (n << lgL); e += NT) {
     const int j = e >> lgL, i = e & (L - 1);
-    sm[e] = src[j * stride + i];
+    sm[sp(e)] = src[j * stride + i];
   }
   __syncthreads();
 }
@@ -83,7 +83,7 @@ __device__ __forceinline__ void lines_store(const C2<T>* sm, C2<T>* dst, long lo
   const int L = 1 << lgL;
   for (int e = threadIdx.x; e < (n << lgL); e += NT) {
     const int j = e >> lgL, i = e & (L - 1);
-    dst[j * stride + i] = sm[e];
+    dst[j * stride + i] = sm[sp(e)];
   }
   __syncthreads();
 }
