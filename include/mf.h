@@ -167,6 +167,24 @@ mf_status mf_get_log(mf_problem* pb, mf_step_log* out, long long cap, long long*
 const char* mf_last_error(const mf_problem* pb);
 void mf_destroy(mf_problem* pb);
 
+/* Film right-hand side that allocates nothing.  (The paper has no counterpart: this is a
+   service for callers that cannot allocate device memory, such as an application that owns
+   all device memory through its own pool and forbids cudaMalloc, or a latency-critical loop
+   that must not take an allocation's implicit device synchronisation.)
+   Evaluates f(t, y) like mf_rhs for a thin film (p->dim == 2) described by p, on `stream`,
+   without a problem handle or a caller workspace: all intermediate buffers live in one static
+   device array of 8 MiB that every GPU loading this library holds until the process exits.
+   Limits: p->nx, p->ny <= 256, otherwise MF_ERR_WORKSPACE with a message in err.
+   d_y, d_ydot: device float64, nx*ny values; force_iters as in mf_rhs_ex; *iters_out (may be
+   NULL) gets the outside iterations; err (may be NULL) gets err_len bytes of message.
+   The first call on a device looks up the array's device address with that device current;
+   make that first call before any stream capture.  Every call shares the array and leaves
+   its contents behind; each call restarts the outside iteration cold (no warm start), and
+   calls whose GPU work overlaps in time race on the array.  The call synchronises `stream`. */
+mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const double* d_y, double* d_ydot,
+                              int force_iters, void* stream, int* iters_out, char* err,
+                              size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

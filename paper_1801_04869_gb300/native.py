@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_NOCONV
 EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf_rhs_ex",
            "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
-           "mf_last_error", "mf_destroy"]
+           "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc"]
 
 
 class mf_params(ctypes.Structure):
@@ -94,6 +94,8 @@ def load() -> ctypes.CDLL:
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
+        "mf_film_rhs_noalloc": (ctypes.c_int, [P(mf_params), ctypes.c_double, vp, vp, ctypes.c_int,
+                                               vp, ip, ctypes.c_char_p, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +261,22 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int = 0,
+                        stream=None):
+    """Film right-hand side through the entry point that allocates nothing (static scratch).
+
+    For callers that cannot allocate device memory; uses the parameters of `problem` but not
+    its workspace or warm start.  Returns (status, iterations, message)."""
+    lib = load()
+    it = ctypes.c_int(0)
+    msg = ctypes.create_string_buffer(256)
+    s = stream if stream is not None else problem.stream
+    st = lib.mf_film_rhs_noalloc(ctypes.byref(problem.params), t, _dptr(y), _dptr(ydot),
+                                 force_iters, ctypes.c_void_p(s.cuda_stream), ctypes.byref(it),
+                                 msg, 256)
+    return st, it.value, msg.value.decode()
 
 
 def from_workload(wl, **over) -> Problem:
