@@ -1,6 +1,508 @@
-// Bulk (3D) kernel: placeholder until the 3D passes land.
-#include "mf_common.cuh"
+// Bulk (3D) right-hand side in the magnetic-field formulation and its BS23 integrator, as one
+// persistent cooperative kernel.
+//
+// Method: Section 3.1 of Prigozhin & Sokolovsky (arXiv:1801.04869).  The state h has three
+// components (component-major).  A vector "round trip" F^-1[M F(v)] runs as five passes
+// separated by grid barriers:
+//   X   x pass: rows of the real field, R2C along x           -> S1[c][z][kx][y]
+//   Yf  y pass: forward along y                                -> S2[c][kx][ky][z]
+//   Z   z pass: forward along z, the 3x3 multiplier M, inverse along z (in place in S2)
+//   Yi  y pass: inverse along y                                -> S1
+//   X   x pass: C2R along x, epilogue on all three components, and the forward x pass of the
+//       next round trip's input
+// Multipliers: the Gaussian-smoothed curl i G k x (Section 3.1, last paragraph) and the
+// Biot-Savart operator Phi = (i/|k|^2) k x (Eq. 17, 1/|k|^2 -> 0 at k = 0).
+// One right-hand side (Eqs. 13-14 and the iteration of Eq. 18):
+//   j = curl h;  e = rho(|j|) j (Eq. 13) or rho_out j;  h_dot_in = -curl e on the conductor
+//   repeat: j_dot = curl h_dot, kept on the conductor;  h_dot_out = h_e_dot + Phi[j_dot] on
+//   free space;  stop when mean_out |h_dot^{i+1} - h_dot^i| < delta_it max(|h_e_dot|, 1).
+#include "mf_rhs_common.cuh"
+
 namespace mf {
-int bulk_max_blocks(int, size_t) { return 0; }
-cudaError_t bulk_launch(int, const Desc&, const KernelArgs&, cudaStream_t) { return cudaErrorNotSupported; }
+
+enum Op3 { OP3_CURL = 0, OP3_CURLNEG = 1, OP3_PHI = 2 };
+
+template <typename T>
+struct Bulk {
+  const Desc& d;
+  C2<T>* sm;
+  C2<T>* sm2;
+  Shared& sh;
+  int nx, ny, nz, lgx, lgy, lgz, half, nkx;
+  long long nspec, ncell;
+  C2<T>* S1;
+  C2<T>* S2;
+  T* hd;
+  const uint8_t* mask;
+  const T* jcmap;
+  const C2<T>* twx; const C2<T>* twy; const C2<T>* twz;
+  const T* ktab; const T* gtab;     // kx (nkx), ky (ny), kz (nz)
+  int rb, zs, P;
+  unsigned nblocks;
+
+  __device__ Bulk(const Desc& dd, C2<T>* s, Shared& shr)
+      : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
+    nx = d.nx; ny = d.ny; nz = d.nz; lgx = d.lgx; lgy = d.lgy; lgz = d.lgz;
+    half = nx / 2; nkx = half + 1;
+    nspec = (long long)nkx * ny * nz;
+    ncell = (long long)nx * ny * nz;
+    S1 = (C2<T>*)d.Sa; S2 = (C2<T>*)d.Sb;
+    hd = (T*)d.hd;
+    mask = d.mask; jcmap = (const T*)d.jcmap;
+    twx = (const C2<T>*)d.tw_x; twy = (const C2<T>*)d.tw_y; twz = (const C2<T>*)d.tw_z;
+    ktab = (const T*)d.ktab; gtab = (const T*)d.gtab;
+    rb = d.rows_per_item;
+    zs = d.zs_per_item;
+    P = BATCH / (3 * nz);
+    if (P > ny) P = ny;
+    int p2 = 1;
+    while (p2 * 2 <= P) p2 *= 2;
+    P = p2;
+    nblocks = gridDim.x;
+  }
+
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
+
+  // ---- x pass over rows (z, y0 .. y0 + rb): inverse of NIN = 0|3 fields, epilogue, forward ----
+  template <int NIN, int NOUT, class Epi>
+  __device__ void xitem(int z, int y0, Epi& epi) {
+    const int npair = rb / 2;
+    const long long off = (long long)z * nkx * ny + y0;
+    C2<T>* X = sm;
+    if (NIN > 0) X = rows_gather_inverse<T>(sm, sm2, S1 + off, nspec, ny, NIN, npair, lgx, twx);
+    C2<T>* Y = X == sm ? sm2 : sm;
+    for (int e = threadIdx.x; e < (npair << lgx); e += NT) {
+      const int pr = e >> lgx, x = e & (nx - 1);
+      T ina[3], inb[3], oa[3], ob[3];
+#pragma unroll
+      for (int f = 0; f < NIN; ++f) {
+        const C2<T> v = X[sp(((f * npair + pr) << lgx) + x)];
+        ina[f] = v.x; inb[f] = v.y;
+      }
+      const long long i0 = ((long long)z * ny + y0 + 2 * pr) * nx + x;
+      epi(i0, ina, oa);
+      epi(i0 + nx, inb, ob);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) X[sp(((f * npair + pr) << lgx) + x)] = C2<T>{oa[f], ob[f]};
+    }
+    __syncthreads();
+    if (NOUT > 0) rows_forward_scatter<T>(X, Y, S1 + off, nspec, ny, NOUT, npair, lgx, twx);
+  }
+  template <int NIN, int NOUT, class Epi>
+  __device__ void xpass(Epi& epi, int slot) {
+    const int per_z = ny / rb;
+    const int nitems = per_z * nz;
+    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+      epi.acc = 0.0;
+      epi.accmax = 0.0;
+      xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
+      if (slot >= 0) {
+        const double v = epi.is_max ? block_max(epi.accmax, sh.red) : block_sum(epi.acc, sh.red);
+        if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
+      }
+    }
+  }
+  __device__ double total(int slot, bool is_max = false) {
+    return reduce_partials(d.partials, d.max_items, slot, (ny / rb) * nz, is_max, sh.red);
+  }
+
+  // ---- y pass, forward: S1[c][z][kx][:] -> S2[c][kx][:][z] for z in [z0, z0 + zs) ----
+  __device__ void yfwd() {
+    const int per_kx = nz / zs;
+    const int nitems = nkx * per_kx;
+    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+      const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+      const int nl = 3 * zs;
+      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+        const int l = e >> lgy, y = e & (ny - 1);
+        const int c = l / zs, dz = l - c * zs;
+        sm[sp(e)] = S1[c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y];
+      }
+      __syncthreads();
+      const C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nl, twy);
+      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+        const int dz = e % zs, rest = e / zs;
+        const int ky = rest & (ny - 1), c = rest >> lgy;
+        S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz] = X[sp(((c * zs + dz) << lgy) + ky)];
+      }
+      __syncthreads();
+    }
+  }
+  // ---- y pass, inverse: S2 -> S1 ----
+  __device__ void yinv() {
+    const int per_kx = nz / zs;
+    const int nitems = nkx * per_kx;
+    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+      const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+      const int nl = 3 * zs;
+      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+        const int dz = e % zs, rest = e / zs;
+        const int ky = rest & (ny - 1), c = rest >> lgy;
+        sm[sp(((c * zs + dz) << lgy) + ky)] = S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz];
+      }
+      __syncthreads();
+      const C2<T>* X = fft_lines<T, +1>(sm, sm2, lgy, nl, twy);
+      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+        const int l = e >> lgy, y = e & (ny - 1);
+        const int c = l / zs, dz = l - c * zs;
+        S1[c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y] = X[sp(e)];
+      }
+      __syncthreads();
+    }
+  }
+  // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
+  __device__ void zpass(int op) {
+    const int per_kx = ny / P;
+    const int nitems = nkx * per_kx;
+    const T s = (T)1 / (T)ncell;
+    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+      const int kx = it / per_kx, ky0 = (it % per_kx) * P;
+      const long long base = ((long long)kx * ny + ky0) * nz;
+      const int pl = P << lgz;                       // values per component
+      for (int e = threadIdx.x; e < 3 * pl; e += NT) {
+        const int c = e / pl, r = e - c * pl;
+        sm[sp(e)] = S2[c * nspec + base + r];
+      }
+      __syncthreads();
+      C2<T>* X = fft_lines<T, -1>(sm, sm2, lgz, 3 * P, twz);
+      C2<T>* Y = X == sm ? sm2 : sm;
+      const T kxv = ktab[kx], gx = gtab[kx];
+      const T kxo = kx == half ? (T)0 : kxv;
+      for (int e = threadIdx.x; e < pl; e += NT) {
+        const int p = e >> lgz, kz = e & (nz - 1);
+        const int ky = ky0 + p;
+        const T kyv = ktab[nkx + ky], kzv = ktab[nkx + ny + kz];
+        const T kyo = ky == ny / 2 ? (T)0 : kyv;
+        const T kzo = kz == nz / 2 ? (T)0 : kzv;
+        const C2<T> a = X[sp(e)], b = X[sp(pl + e)], c = X[sp(2 * pl + e)];
+        // cross product k x v with the odd (Nyquist-free) wavenumbers
+        C2<T> cx = {kyo * c.x - kzo * b.x, kyo * c.y - kzo * b.y};
+        C2<T> cy = {kzo * a.x - kxo * c.x, kzo * a.y - kxo * c.y};
+        C2<T> cz = {kxo * b.x - kyo * a.x, kxo * b.y - kyo * a.y};
+        T f;
+        if (op == OP3_PHI) {
+          const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+          f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
+        } else {
+          const T G = gx * gtab[nkx + ky] * gtab[nkx + ny + kz];
+          f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
+        }
+        X[sp(e)] = cmul_si(cscale(cx, f), 1);
+        X[sp(pl + e)] = cmul_si(cscale(cy, f), 1);
+        X[sp(2 * pl + e)] = cmul_si(cscale(cz, f), 1);
+      }
+      __syncthreads();
+      const C2<T>* Z = fft_lines<T, +1>(X, Y, lgz, 3 * P, twz);
+      for (int e = threadIdx.x; e < 3 * pl; e += NT) {
+        const int c = e / pl, r = e - c * pl;
+        S2[c * nspec + base + r] = Z[sp(e)];
+      }
+      __syncthreads();
+    }
+  }
+
+  // Yf, Z(op), Yi with barriers; the x passes before and after are separate
+  __device__ bool yzy(int op, int where) {
+    yfwd();
+    if (!sync(where)) return false;
+    zpass(op);
+    if (!sync(where + 1)) return false;
+    yinv();
+    return sync(where + 2);
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// epilogues of the x pass (cell index i, three components in / out)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct BStage : EpiBase<T> {
+  const Bulk<T>* B;
+  StageIn in;
+  __device__ void operator()(long long i, const T*, T* out) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long k = c * B->ncell + i;
+      double v = in.y[k];
+      for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][k];
+      if (in.ynew) in.ynew[k] = v;
+      out[c] = (T)v;
+    }
+  }
+};
+
+template <typename T>
+struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law)
+  const Bulk<T>* B;
+  T n, e0, jc, rho_out;
+  __device__ void operator()(long long i, const T* in, T* out) {
+    const int m = B->mask[i];
+    const T jcl = B->jcmap ? B->jcmap[i] : jc;
+    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
+    out[0] = rho * in[0]; out[1] = rho * in[1]; out[2] = rho * in[2];
+  }
+};
+
+template <typename T>
+struct BInit : EpiBase<T> {                // h_dot^0: h_dot_in on the conductor, warm or h_e_dot outside
+  const Bulk<T>* B;
+  bool warm;
+  T hed[3];
+  __device__ void operator()(long long i, const T* in, T* out) {
+    const bool cond = B->mask[i] != 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T h;
+      if (cond) h = in[c];                                 // -curl e (Eq. 14)
+      else h = warm ? B->hd[c * B->ncell + i] : hed[c];
+      B->hd[c * B->ncell + i] = h;
+      out[c] = h;
+    }
+  }
+};
+
+template <typename T>
+struct BMaskCond : EpiBase<T> {            // j_dot_in: keep on the conductor only
+  const Bulk<T>* B;
+  __device__ void operator()(long long i, const T* in, T* out) {
+    const bool cond = B->mask[i] != 0;
+    out[0] = cond ? in[0] : (T)0; out[1] = cond ? in[1] : (T)0; out[2] = cond ? in[2] : (T)0;
+  }
+};
+
+template <typename T>
+struct BUpdate : EpiBase<T> {              // Eq. 18 on free space, residual, forward
+  const Bulk<T>* B;
+  T hed[3];
+  __device__ void operator()(long long i, const T* in, T* out) {
+    if (B->mask[i] == 0) {
+      double s2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T hn = hed[c] + in[c];
+        const T ho = B->hd[c * B->ncell + i];
+        const double df = (double)hn - (double)ho;
+        s2 += df * df;
+        B->hd[c * B->ncell + i] = hn;
+        out[c] = hn;
+      }
+      this->acc += sqrt(s2);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = B->hd[c * B->ncell + i];
+    }
+  }
+};
+
+template <typename T>
+struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 error contribution
+  const Bulk<T>* B;
+  double* kout;
+  bool err;
+  double h, rtol, atol;
+  const double* k1; const double* k2; const double* k3; const double* y; const double* ynew;
+  __device__ void operator()(long long i, const T*, T*) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long k = c * B->ncell + i;
+      const double g = (double)B->hd[k];
+      kout[k] = g;
+      if (err) {
+        const double E = h * (-5.0 / 72.0 * k1[k] + 1.0 / 12.0 * k2[k] + 1.0 / 9.0 * k3[k] - 0.125 * g);
+        const double sc = atol + rtol * fmax(fabs(y[k]), fabs(ynew[k]));
+        double q = fabs(E) / sc;
+        if (!(q == q) || isinf(q)) q = 1e300;
+        this->accmax = fmax(this->accmax, q);
+      } else if (!isfinite(g)) {
+        this->accmax = 1.0;
+      }
+    }
+  }
+};
+
+template <typename T>
+struct BStoreJ : EpiBase<T> {              // readout of j = curl h (FP64)
+  const Bulk<T>* B;
+  double* out;
+  __device__ void operator()(long long i, const T* in, T*) {
+    out[i] = in[0]; out[B->ncell + i] = in[1]; out[2 * B->ncell + i] = in[2];
+  }
+};
+
+template <typename T>
+struct BMoment : EpiBase<T> {              // m = 1/2 sum dV r x j over the conductor, component `comp`
+  const Bulk<T>* B;
+  int comp;
+  __device__ void operator()(long long i, const T* in, T*) {
+    if (B->mask[i] == 0) return;
+    const int x = (int)(i % B->nx), y = (int)((i / B->nx) % B->ny), z = (int)(i / ((long long)B->nx * B->ny));
+    const double rx = -B->d.Lx + (x + 0.5) * B->d.dx;
+    const double ry = -B->d.Ly + (y + 0.5) * B->d.dy;
+    const double rz = -B->d.Lz + (z + 0.5) * B->d.dz;
+    double v;
+    if (comp == 0) v = ry * in[2] - rz * in[1];
+    else if (comp == 1) v = rz * in[0] - rx * in[2];
+    else v = rx * in[1] - ry * in[0];
+    this->acc += v;
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// one bulk right-hand side
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ RhsOut bulk_rhs(Bulk<T>& B, double t, int seg, const StageIn& sin, double* kout,
+                                        int force_iters, bool want_err, double h_err, const double* e_k1,
+                                        const double* e_k2, const double* e_k3, const double* e_y,
+                                        const double* e_ynew) {
+  const Desc& d = B.d;
+  RhsOut res{ST_OK, 0, 0.0, 0.0, 0};
+  const double hs = he_dot(d, t, seg);
+  const double hed[3] = {hs * d.he_dir[0], hs * d.he_dir[1], hs * d.he_dir[2]};
+  const double hed_norm = sqrt(hed[0] * hed[0] + hed[1] * hed[1] + hed[2] * hed[2]);
+#define BSYNC(w) if (!B.sync(w)) { res.status = ST_BARRIER; return res; }
+#define BYZY(op, w) if (!B.yzy(op, w)) { res.status = ST_BARRIER; return res; }
+  { BStage<T> e; e.B = &B; e.in = sin; B.xpass<0, 3>(e, -1); }
+  BSYNC(101);
+  BYZY(OP3_CURL, 102);                                                   // j = curl h
+  {
+    BPower<T> e; e.B = &B; e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+    B.xpass<3, 3>(e, -1);                                                // e = rho j
+  }
+  BSYNC(105);
+  BYZY(OP3_CURLNEG, 106);                                                // -curl e
+  {
+    BInit<T> e; e.B = &B; e.warm = B.sh.warm_valid != 0;
+    for (int c = 0; c < 3; ++c) e.hed[c] = (T)hed[c];
+    B.xpass<3, 3>(e, -1);                                                // h_dot^0
+  }
+  BSYNC(109);
+  const bool have_out = d.nout > 0;
+  const double thresh = d.iter_tol * fmax(hed_norm, 1.0);
+  const bool forced = force_iters > 0;
+  const bool fixed = d.iter_tol <= 0.0;
+  const int itmax = forced ? force_iters : d.iter_max;
+  double r = 0.0;
+  int i = 0;
+  if (have_out) {
+    for (; i < itmax; ++i) {
+      BYZY(OP3_CURL, 110);                                               // j_dot = curl h_dot
+      { BMaskCond<T> e; e.B = &B; B.xpass<3, 3>(e, -1); }                // j_dot_in
+      BSYNC(113);
+      BYZY(OP3_PHI, 114);                                                // Phi[j_dot_in]
+      {
+        BUpdate<T> e; e.B = &B;
+        for (int c = 0; c < 3; ++c) e.hed[c] = (T)hed[c];
+        B.xpass<3, 3>(e, 0);                                             // Eq. 18
+      }
+      BSYNC(117);
+      r = B.total(0) / (double)d.nout;
+      if (!(forced || fixed) && r < thresh) { ++i; break; }
+    }
+    if (i > itmax) i = itmax;
+  }
+  res.iters = i;
+  res.r = r;
+  res.status = (!have_out || fixed || r < thresh) ? ST_OK : ST_NOCONV;
+  B.sh.warm_valid = 1;
+  {
+    BFinal<T> e; e.B = &B; e.kout = kout; e.is_max = true;
+    e.err = want_err; e.h = h_err; e.rtol = d.rtol; e.atol = d.atol;
+    e.k1 = e_k1; e.k2 = e_k2; e.k3 = e_k3; e.y = e_y; e.ynew = e_ynew;
+    B.xpass<0, 0>(e, 3);
+  }
+  BSYNC(120);
+  const double q = B.total(3, true);
+  if (want_err) res.err = q;
+  else res.nonfinite = q > 0.0;
+#undef BSYNC
+#undef BYZY
+  return res;
+}
+
+template <typename T>
+struct BulkRhs {
+  Bulk<T>& B;
+  __device__ RhsOut operator()(double t, int seg, const StageIn& in, double* kout, int force,
+                               bool want_err, double h, const double* k1, const double* k2,
+                               const double* k3, const double* y, const double* yn) {
+    return bulk_rhs<T>(B, t, seg, in, kout, force, want_err, h, k1, k2, k3, y, yn);
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sm = (C2<T>*)smraw;
+  __shared__ Shared sh;
+  SolverState* st = d.st;
+  if (threadIdx.x == 0) {
+    sh.warm_valid = st->warm_valid;
+    sh.A_prev = 0.0;
+  }
+  __syncthreads();
+  Bulk<T> B(d, sm, sh);
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  int status = ST_OK;
+
+  if (a.mode == MODE_RHS) {
+    StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    RhsOut r = bulk_rhs<T>(B, a.t, a.seg, in, a.out, a.force_iters, false, 0.0, nullptr, nullptr,
+                           nullptr, nullptr, nullptr);
+    status = r.status == ST_OK && r.nonfinite ? ST_NONFINITE : r.status;
+    if (leader) { st->last_iters = r.iters; st->last_r = r.r; st->n_rhs += 1; st->n_iters += r.iters; }
+  } else if (a.mode == MODE_J || a.mode == MODE_MOMENT) {
+    StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    { BStage<T> e; e.B = &B; e.in = in; B.xpass<0, 3>(e, -1); }
+    bool ok = B.sync(201) && B.yzy(OP3_CURL, 202);
+    if (ok) {
+      if (a.mode == MODE_J) {
+        BStoreJ<T> e; e.B = &B; e.out = a.out;
+        B.xpass<3, 0>(e, -1);
+      } else {
+        for (int c = 0; c < 3 && ok; ++c) {
+          BMoment<T> e; e.B = &B; e.comp = c;
+          B.xpass<3, 0>(e, 4 + c);      // reads S1 only, so the three passes share it
+        }
+        ok = B.sync(205);
+        if (ok) {
+          for (int c = 0; c < 3; ++c) {
+            const double s = B.total(4 + c);
+            if (leader) a.out[c] = 0.5 * s * d.dx * d.dy * d.dz;
+          }
+        }
+      }
+    }
+    if (!ok) status = ST_BARRIER;
+  } else if (a.mode == MODE_ADVANCE) {
+    BulkRhs<T> R{B};
+    status = bs23_advance(R, d, st, a, leader);
+  }
+  if (leader) {
+    st->warm_valid = sh.warm_valid;
+    st->status = status;
+  }
+}
+
+int bulk_max_blocks(int precision, size_t smem) {
+  int nb = 0;
+  if (precision) {
+    cudaFuncSetAttribute(bulk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bulk_kernel<float>, NT, smem);
+  } else {
+    cudaFuncSetAttribute(bulk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bulk_kernel<double>, NT, smem);
+  }
+  return nb;
+}
+
+cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s) {
+  Desc dd = d;
+  KernelArgs aa = a;
+  void* args[] = {&dd, &aa};
+  const size_t smem = kernel_smem_bytes(precision);
+  const void* fn = precision ? (const void*)bulk_kernel<float> : (const void*)bulk_kernel<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);
+}
+
 }  // namespace mf
