@@ -249,7 +249,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   pb->scratch_m = (double*)(w + L.mscr);
 
   // launch configuration: all CTAs co-resident, no more than the widest pass can use
-  const size_t smem = kernel_smem_bytes(p->precision);
+  const size_t smem = kernel_smem_bytes(d);
   int per_sm = p->dim == 2 ? film_max_blocks(p->precision, smem) : bulk_max_blocks(p->precision, smem);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pb->device);
@@ -497,7 +497,7 @@ mf_status mf_get_info(mf_problem* pb, mf_info* out) {
   out->log_count = s.log_count; out->last_iters = s.last_iters;
   out->last_r = s.last_r; out->last_err = s.last_err;
   out->grid = pb->d.grid; out->threads = NT;
-  out->smem_bytes = (int)kernel_smem_bytes(pb->d.precision);
+  out->smem_bytes = (int)kernel_smem_bytes(pb->d);
   out->rows_per_item = pb->d.rows_per_item;
   out->workspace_used = (long long)pb->used;
   return MF_OK;

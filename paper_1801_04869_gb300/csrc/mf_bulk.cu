@@ -39,6 +39,7 @@ struct Bulk {
   const T* ktab; const T* gtab;     // kx (nkx), ky (ny), kz (nz)
   int rb, zs, P;
   unsigned nblocks;
+  WorkQueue wq;
 
   __device__ Bulk(const Desc& dd, C2<T>* s, Shared& shr)
       : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
@@ -49,7 +50,9 @@ struct Bulk {
     S1 = (C2<T>*)d.Sa; S2 = (C2<T>*)d.Sb;
     hd = (T*)d.hd;
     mask = d.mask; jcmap = (const T*)d.jcmap;
-    twx = (const C2<T>*)d.tw_x; twy = (const C2<T>*)d.tw_y; twz = (const C2<T>*)d.tw_z;
+    twx = sm + 2 * BATCH_PAD;                   // twiddle tables copied to shared memory
+    twy = twx + nx;
+    twz = twy + ny;
     ktab = (const T*)d.ktab; gtab = (const T*)d.gtab;
     rb = d.rows_per_item;
     zs = d.zs_per_item;
@@ -59,6 +62,7 @@ struct Bulk {
     while (p2 * 2 <= P) p2 *= 2;
     P = p2;
     nblocks = gridDim.x;
+    wq.base = 0;
   }
 
   __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
@@ -69,8 +73,10 @@ struct Bulk {
     const int npair = rb / 2;
     const long long off = (long long)z * nkx * ny + y0;
     C2<T>* X = sm;
-    if (NIN > 0) X = rows_gather_inverse<T>(sm, sm2, S1 + off, nspec, ny, NIN, npair, lgx, twx);
+    const int lgpair = __ffs(npair) - 1;
+    if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(sm, sm2, S1 + off, nspec, ny, npair, lgpair, lgx, twx);
     C2<T>* Y = X == sm ? sm2 : sm;
+#pragma unroll 2
     for (int e = threadIdx.x; e < (npair << lgx); e += NT) {
       const int pr = e >> lgx, x = e & (nx - 1);
       T ina[3], inb[3], oa[3], ob[3];
@@ -86,13 +92,13 @@ struct Bulk {
       for (int f = 0; f < NOUT; ++f) X[sp(((f * npair + pr) << lgx) + x)] = C2<T>{oa[f], ob[f]};
     }
     __syncthreads();
-    if (NOUT > 0) rows_forward_scatter<T>(X, Y, S1 + off, nspec, ny, NOUT, npair, lgx, twx);
+    if constexpr (NOUT > 0) rows_forward_scatter<T, NOUT>(X, Y, S1 + off, nspec, ny, npair, lgpair, lgx, twx);
   }
   template <int NIN, int NOUT, class Epi>
   __device__ void xpass(Epi& epi, int slot) {
     const int per_z = ny / rb;
     const int nitems = per_z * nz;
-    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
@@ -101,6 +107,7 @@ struct Bulk {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
+    wq.end_phase(nitems);
   }
   __device__ double total(int slot, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, (ny / rb) * nz, is_max, sh.red);
@@ -110,7 +117,7 @@ struct Bulk {
   __device__ void yfwd() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
@@ -127,12 +134,13 @@ struct Bulk {
       }
       __syncthreads();
     }
+    wq.end_phase(nitems);
   }
   // ---- y pass, inverse: S2 -> S1 ----
   __device__ void yinv() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
@@ -149,13 +157,14 @@ struct Bulk {
       }
       __syncthreads();
     }
+    wq.end_phase(nitems);
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
   __device__ void zpass(int op) {
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
-    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, ky0 = (it % per_kx) * P;
       const long long base = ((long long)kx * ny + ky0) * nz;
       const int pl = P << lgz;                       // values per component
@@ -199,6 +208,7 @@ struct Bulk {
       }
       __syncthreads();
     }
+    wq.end_phase(nitems);
   }
 
   // Yf, Z(op), Yi with barriers; the x passes before and after are separate
@@ -236,8 +246,8 @@ struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law)
   const Bulk<T>* B;
   T n, e0, jc, rho_out;
   __device__ void operator()(long long i, const T* in, T* out) {
-    const int m = B->mask[i];
-    const T jcl = B->jcmap ? B->jcmap[i] : jc;
+    const int m = __ldg(&B->mask[i]);
+    const T jcl = B->jcmap ? __ldg(&B->jcmap[i]) : jc;
     const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
     out[0] = rho * in[0]; out[1] = rho * in[1]; out[2] = rho * in[2];
   }
@@ -249,7 +259,7 @@ struct BInit : EpiBase<T> {                // h_dot^0: h_dot_in on the conductor
   bool warm;
   T hed[3];
   __device__ void operator()(long long i, const T* in, T* out) {
-    const bool cond = B->mask[i] != 0;
+    const bool cond = __ldg(&B->mask[i]) != 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       T h;
@@ -265,7 +275,7 @@ template <typename T>
 struct BMaskCond : EpiBase<T> {            // j_dot_in: keep on the conductor only
   const Bulk<T>* B;
   __device__ void operator()(long long i, const T* in, T* out) {
-    const bool cond = B->mask[i] != 0;
+    const bool cond = __ldg(&B->mask[i]) != 0;
     out[0] = cond ? in[0] : (T)0; out[1] = cond ? in[1] : (T)0; out[2] = cond ? in[2] : (T)0;
   }
 };
@@ -275,7 +285,7 @@ struct BUpdate : EpiBase<T> {              // Eq. 18 on free space, residual, fo
   const Bulk<T>* B;
   T hed[3];
   __device__ void operator()(long long i, const T* in, T* out) {
-    if (B->mask[i] == 0) {
+    if (__ldg(&B->mask[i]) == 0) {
       double s2 = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -334,7 +344,7 @@ struct BMoment : EpiBase<T> {              // m = 1/2 sum dV r x j over the cond
   const Bulk<T>* B;
   int comp;
   __device__ void operator()(long long i, const T* in, T*) {
-    if (B->mask[i] == 0) return;
+    if (__ldg(&B->mask[i]) == 0) return;
     const int x = (int)(i % B->nx), y = (int)((i / B->nx) % B->ny), z = (int)(i / ((long long)B->nx * B->ny));
     const double rx = -B->d.Lx + (x + 0.5) * B->d.dx;
     const double ry = -B->d.Ly + (y + 0.5) * B->d.dy;
@@ -441,6 +451,10 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
     sh.A_prev = 0.0;
   }
   __syncthreads();
+  table_to_smem<T>(sm + 2 * BATCH_PAD, (const C2<T>*)d.tw_x, d.nx);
+  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx, (const C2<T>*)d.tw_y, d.ny);
+  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx + d.ny, (const C2<T>*)d.tw_z, d.nz);
+  __syncthreads();
   Bulk<T> B(d, sm, sh);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int status = ST_OK;
@@ -462,9 +476,9 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
       } else {
         for (int c = 0; c < 3 && ok; ++c) {
           BMoment<T> e; e.B = &B; e.comp = c;
-          B.xpass<3, 0>(e, 4 + c);      // reads S1 only, so the three passes share it
+          B.xpass<3, 0>(e, 4 + c);      // reads S1 only
+          ok = B.sync(205 + c);
         }
-        ok = B.sync(205);
         if (ok) {
           for (int c = 0; c < 3; ++c) {
             const double s = B.total(4 + c);
@@ -500,7 +514,7 @@ cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaS
   Desc dd = d;
   KernelArgs aa = a;
   void* args[] = {&dd, &aa};
-  const size_t smem = kernel_smem_bytes(precision);
+  const size_t smem = kernel_smem_bytes(d);
   const void* fn = precision ? (const void*)bulk_kernel<float> : (const void*)bulk_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);
 }

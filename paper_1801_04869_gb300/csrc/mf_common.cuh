@@ -70,6 +70,28 @@ struct GridBarrier {
   unsigned int gen;
   int abort;
   int where;
+  unsigned long long work;       // work-item counter of the dynamic schedule (monotonic)
+};
+
+// Dynamic schedule of the work items of one phase: CTAs take items from a monotonic counter.
+// Every CTA ends a phase with exactly one failed grab, so after a phase of n items the counter
+// has advanced by n + gridDim.x in every CTA's view; `base` tracks that without a reset.
+struct WorkQueue {
+  unsigned long long base;
+  // next item of the current phase (>= nitems: the phase is done for this CTA).  Phases that
+  // use the schedule must be separated by a grid barrier; a negative index would mean a CTA
+  // grabbed ahead of the others, which raises the abort flag instead of touching memory.
+  __device__ __forceinline__ int next(GridBarrier* gb, int* s_item) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long v = (long long)(atomicAdd(&gb->work, 1ull) - base);
+      if (v < 0) { atomicExch(&gb->abort, 1); v = 0x7fffffff; }
+      *s_item = v > 0x7fffffff ? 0x7fffffff : (int)v;
+    }
+    __syncthreads();
+    return *s_item;
+  }
+  __device__ __forceinline__ void end_phase(int nitems) { base += (unsigned long long)nitems + gridDim.x; }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -251,6 +273,6 @@ cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaS
 cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s);
 int film_max_blocks(int precision, size_t smem);
 int bulk_max_blocks(int precision, size_t smem);
-size_t kernel_smem_bytes(int precision);
+size_t kernel_smem_bytes(const Desc& d);
 
 }  // namespace mf

@@ -1,5 +1,6 @@
-// Shared-memory FFT of a batch of lines (Stockham autosort, radix 8 with one radix-4 or
-// radix-2 stage), the building block of every row, column and z pass.
+// Shared-memory FFT of a batch of lines (Stockham autosort; radix 16 and 8 in single
+// precision, radix 8 in double, with one radix-4 or radix-2 stage), the building block of
+// every row, column and z pass.
 //
 // A CTA of NT threads transforms `nlines` lines of length L (a power of two, 2..4096) that
 // sit back to back in shared memory (element e at position sp(e)), nlines * L <= BATCH.  Stages alternate between two
@@ -25,9 +26,45 @@ __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3)
   a3 = csub(t1, t3);
 }
 
+// multiply by (c + DIR i s)
+template <typename T, int DIR>
+__device__ __forceinline__ C2<T> crot(C2<T> a, T c, T s) {
+  const T ss = (T)DIR * s;
+  return C2<T>{a.x * c - a.y * ss, a.x * ss + a.y * c};
+}
+
+// length-16 DFT as 4 x 4: DFT4 over n1 for each n2, twiddles W16^(n2 k1), DFT4 over n2, and
+// the transpose k1 + 4 k2 -> natural order
+template <typename T, int DIR>
+__device__ __forceinline__ void dft16(C2<T>* v) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, h = Sqrt1_2<T>::v;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<T, DIR>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // slot 4 k1 + n2 holds y[n2][k1]; multiply by W16^(n2 k1), W16^m = cos(m pi/8) + DIR i sin(m pi/8)
+  v[5] = crot<T, DIR>(v[5], c1, s1);                       // n2 = 1, k1 = 1: m = 1
+  v[9] = crot<T, DIR>(v[9], h, h);                         // n2 = 1, k1 = 2: m = 2
+  v[13] = crot<T, DIR>(v[13], s1, c1);                     // n2 = 1, k1 = 3: m = 3
+  v[6] = crot<T, DIR>(v[6], h, h);                         // n2 = 2, k1 = 1: m = 2
+  v[10] = cmul_si(v[10], DIR);                             // n2 = 2, k1 = 2: m = 4
+  v[14] = crot<T, DIR>(v[14], -h, h);                      // n2 = 2, k1 = 3: m = 6
+  v[7] = crot<T, DIR>(v[7], s1, c1);                       // n2 = 3, k1 = 1: m = 3
+  v[11] = crot<T, DIR>(v[11], -h, h);                      // n2 = 3, k1 = 2: m = 6
+  v[15] = crot<T, DIR>(v[15], -c1, -s1);                   // n2 = 3, k1 = 3: m = 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<T, DIR>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // X[k1 + 4 k2] sits in slot 4 k1 + k2
+  C2<T> w[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) w[j] = v[4 * (j & 3) + (j >> 2)];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = w[j];
+}
+
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void dft(C2<T>* v) {
-  if constexpr (R == 2) {
+  if constexpr (R == 16) {
+    dft16<T, DIR>(v);
+  } else if constexpr (R == 2) {
     C2<T> a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
     v[0] = a; v[1] = b;
   } else if constexpr (R == 4) {
@@ -97,7 +134,11 @@ __device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines
   C2<T>* in = a;
   C2<T>* out = b;
   while (rem > 0) {
-    if (rem >= 3) {
+    if (sizeof(T) == 4 && rem >= 4 && rem != 5) {
+      // single precision: radix 16 (three shared-memory passes for 2048 points)
+      fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw);
+      lgp += 4; rem -= 4;
+    } else if (rem >= 3) {
       fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw);
       lgp += 3; rem -= 3;
     } else if (rem == 2) {

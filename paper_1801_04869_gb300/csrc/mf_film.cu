@@ -44,6 +44,7 @@ struct Film {
   const T* gtab;     // Gaussian factors, same layout
   int rb1, rb2;      // rows per item for one- and two-field row passes
   unsigned nblocks;
+  WorkQueue wq;      // dynamic schedule of the work items
 
   __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
     nx = d.nx; ny = d.ny; lgx = d.lgx; lgy = d.lgy; half = nx / 2; nkx = half + 1;
@@ -52,12 +53,14 @@ struct Film {
     Sa = (C2<T>*)d.Sa; Sb = (C2<T>*)d.Sb;
     hd = (T*)d.hd; u = (T*)d.u; q1 = (const T*)d.q1; q2 = (const T*)d.q2;
     mask = d.mask; jcmap = (const T*)d.jcmap;
-    twx = (const C2<T>*)d.tw_x; twy = (const C2<T>*)d.tw_y;
+    twx = sm + 2 * BATCH_PAD;                   // twiddle tables copied to shared memory
+    twy = twx + nx;
     ktab = (const T*)d.ktab;
     gtab = (const T*)d.gtab;
     rb1 = d.rows_per_item;
     rb2 = d.zs_per_item;
     nblocks = gridDim.x;
+    wq.base = 0;
   }
 
   __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
@@ -100,7 +103,9 @@ struct Film {
   }
 
   __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
-    for (int kx = blockIdx.x; kx < nkx; kx += nblocks) col_item(kx, Sin, nin, Sout, nout, op);
+    for (int kx = wq.next(d.gb, &sh.item); kx < nkx; kx = wq.next(d.gb, &sh.item))
+      col_item(kx, Sin, nin, Sout, nout, op);
+    wq.end_phase(nkx);
   }
 
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
@@ -109,30 +114,42 @@ struct Film {
   __device__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi) {
     const int npair = rb / 2;
     C2<T>* X = sm;
-    if (NIN > 0) X = rows_gather_inverse<T>(sm, sm2, Sin + y0, nspec, ny, NIN, npair, lgx, twx);
+    const int lgpair = __ffs(npair) - 1;
+    if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(sm, sm2, Sin + y0, nspec, ny, npair, lgpair, lgx, twx);
     C2<T>* Y = X == sm ? sm2 : sm;
-    for (int e = threadIdx.x; e < (npair << lgx); e += NT) {
-      const int pr = e >> lgx, x = e & (nx - 1);
-      T ina[NIN > 0 ? NIN : 1], inb[NIN > 0 ? NIN : 1], oa[NOUT > 0 ? NOUT : 1], ob[NOUT > 0 ? NOUT : 1];
+    // four consecutive cells of both rows of a pair per step; the epilogue issues its global
+    // loads for the four cells together
+    const int lgq = lgx - 2;
+#pragma unroll 2
+    for (int e = threadIdx.x; e < (npair << lgq); e += NT) {
+      const int pr = e >> lgq, x0 = (e & ((1 << lgq) - 1)) << 2;
+      V4<T> ina[NIN > 0 ? NIN : 1], inb[NIN > 0 ? NIN : 1], oa[NOUT > 0 ? NOUT : 1], ob[NOUT > 0 ? NOUT : 1];
 #pragma unroll
       for (int f = 0; f < NIN; ++f) {
-        const C2<T> z = X[sp(((f * npair + pr) << lgx) + x)];
-        ina[f] = z.x; inb[f] = z.y;
-      }
-      epi(y0 + 2 * pr, x, ina, oa);
-      epi(y0 + 2 * pr + 1, x, inb, ob);
 #pragma unroll
-      for (int f = 0; f < NOUT; ++f) X[sp(((f * npair + pr) << lgx) + x)] = C2<T>{oa[f], ob[f]};
+        for (int j = 0; j < 4; ++j) {
+          const C2<T> z = X[sp(((f * npair + pr) << lgx) + x0 + j)];
+          ina[f].v[j] = z.x; inb[f].v[j] = z.y;
+        }
+      }
+      const long long i0 = (long long)(y0 + 2 * pr) * nx + x0;
+      epi(i0, ina, oa);
+      epi(i0 + nx, inb, ob);
+#pragma unroll
+      for (int f = 0; f < NOUT; ++f) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) X[sp(((f * npair + pr) << lgx) + x0 + j)] = C2<T>{oa[f].v[j], ob[f].v[j]};
+      }
     }
     __syncthreads();
-    if (NOUT > 0) rows_forward_scatter<T>(X, Y, Sout + y0, nspec, ny, NOUT, npair, lgx, twx);
+    if constexpr (NOUT > 0) rows_forward_scatter<T, NOUT>(X, Y, Sout + y0, nspec, ny, npair, lgpair, lgx, twx);
   }
 
   // rows pass with an optional per-item reduction into partials slot `slot`
   template <int NIN, int NOUT, class Epi>
   __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
     const int nitems = ny / rb;
-    for (int it = blockIdx.x; it < nitems; it += nblocks) {
+    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
@@ -141,6 +158,7 @@ struct Film {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
+    wq.end_phase(nitems);
   }
   __device__ double total(int slot, int rb, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, ny / rb, is_max, sh.red);
@@ -150,18 +168,24 @@ struct Film {
 // ------------------------------------------------------------------------------------------
 // epilogues
 // ------------------------------------------------------------------------------------------
+// Epilogues of the x pass: called with the index i of the first of four consecutive cells of
+// one row, the inverse-transformed inputs in[f].v[0..3] and outputs out[f].v[0..3].
+
 // P1 / readouts: field from the FP64 stage input
 template <typename T>
 struct EpiStage : EpiBase<T> {
   const Film<T>* F;
   StageIn in;
-  __device__ void operator()(int y, int x, const T*, T* out) {
-    const long long i = (long long)y * F->nx + x;
-    double v = in.y[i];
-    for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][i];
-    if (in.ynew) in.ynew[i] = v;
-    this->acc += v;
-    out[0] = (T)v;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
+    V4<double> v = ld4(in.y + i);
+    for (int j = 0; j < in.nk; ++j) {
+      const V4<double> k = ld4(in.k[j] + i);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v.v[q] += in.c[j] * k.v[q];
+    }
+    if (in.ynew) st4(in.ynew + i, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { this->acc += v.v[q]; out[0].v[q] = (T)v.v[q]; }
   }
 };
 
@@ -169,27 +193,31 @@ struct EpiStage : EpiBase<T> {
 template <typename T>
 struct EpiOut : EpiBase<T> {
   const Film<T>* F;
-  __device__ void operator()(int y, int x, const T*, T* out) {
-    out[0] = F->mask[(long long)y * F->nx + x] == 0 ? (T)1 : (T)0;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
+    const uchar4 m = ldmask4(F->mask + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[0].v[q] = mask_at(m, q) == 0 ? (T)1 : (T)0;
   }
 };
 
-// store a real field (set-up, readouts)
+// store a real field (set-up)
 template <typename T>
 struct EpiStoreT : EpiBase<T> {
   const Film<T>* F;
   T* dst;
-  __device__ void operator()(int y, int x, const T* in, T*) {
-    dst[(long long)y * F->nx + x] = in[0];
-  }
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) { st4(dst + i, in[0]); }
 };
+// h_z readout (FP64)
 template <typename T>
 struct EpiStoreHz : EpiBase<T> {
   const Film<T>* F;
   double* dst;
   double he;
-  __device__ void operator()(int y, int x, const T* in, T*) {
-    dst[(long long)y * F->nx + x] = he + (double)in[0];
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
+    V4<double> o;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o.v[q] = he + (double)in[0].v[q];
+    st4(dst + i, o);
   }
 };
 
@@ -198,15 +226,19 @@ template <typename T>
 struct EpiPower : EpiBase<T> {
   const Film<T>* F;
   T n, e0, jc, rho_out;
-  __device__ void operator()(int y, int x, const T* in, T* out) {
-    const long long i = (long long)y * F->nx + x;
-    const T gx = in[0], gy = in[1];
-    const T jx = gy, jy = -gx;                              // Eq. 2
-    const int m = F->mask[i];
-    const T jcl = F->jcmap ? F->jcmap[i] : jc;
-    const T rho = resistivity<T>(jx * jx + jy * jy, jcl, m, n, e0, rho_out);
-    out[0] = rho * jx;                                      // Eq. 3
-    out[1] = rho * jy;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(F->mask + i);
+    V4<T> jcl;
+    if (F->jcmap) jcl = ldg4(F->jcmap + i);
+    else jcl = V4<T>{{jc, jc, jc, jc}};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T gx = in[0].v[q], gy = in[1].v[q];
+      const T jx = gy, jy = -gx;                              // Eq. 2
+      const T rho = resistivity<T>(jx * jx + jy * jy, jcl.v[q], mask_at(m, q), n, e0, rho_out);
+      out[0].v[q] = rho * jx;                                 // Eq. 3
+      out[1].v[q] = rho * jy;
+    }
   }
 };
 
@@ -216,14 +248,18 @@ struct EpiInit : EpiBase<T> {
   const Film<T>* F;
   bool warm;
   T A_prev, hed;
-  __device__ void operator()(int y, int x, const T* in, T* out) {
-    const long long i = (long long)y * F->nx + x;
-    const int m = F->mask[i];
-    T h;
-    if (m != 0) h = in[0];                                  // h_dot_in on the conductor
-    else h = warm ? F->hd[i] - A_prev : hed;                // warm start (Section 2.2)
-    F->hd[i] = h;
-    this->acc += (double)h;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(F->mask + i);
+    V4<T> w;
+    if (warm) w = ld4(F->hd + i);
+    V4<T> h;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (mask_at(m, q) != 0) h.v[q] = in[0].v[q];             // h_dot_in on the conductor
+      else h.v[q] = warm ? w.v[q] - A_prev : hed;             // warm start (Section 2.2)
+      this->acc += (double)h.v[q];
+    }
+    st4(F->hd + i, h);
     out[0] = h;
   }
 };
@@ -233,13 +269,18 @@ template <typename T>
 struct EpiU : EpiBase<T> {
   const Film<T>* F;
   T A;
-  __device__ void operator()(int y, int x, const T* in, T* out) {
-    const long long i = (long long)y * F->nx + x;
-    const T v = in[0] - A * F->q1[i];
-    F->u[i] = v;
-    const bool o = F->mask[i] == 0;
-    if (o) this->acc += (double)v;
-    out[0] = o ? v : (T)0;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(F->mask + i);
+    const V4<T> q1 = ldg4(F->q1 + i);
+    V4<T> v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v.v[q] = in[0].v[q] - A * q1.v[q];
+      const bool o = mask_at(m, q) == 0;
+      if (o) this->acc += (double)v.v[q];
+      out[0].v[q] = o ? v.v[q] : (T)0;
+    }
+    st4(F->u + i, v);
   }
 };
 
@@ -248,9 +289,12 @@ template <typename T>
 struct EpiResid : EpiBase<T> {
   const Film<T>* F;
   double C;
-  __device__ void operator()(int y, int x, const T*, T*) {
-    const long long i = (long long)y * F->nx + x;
-    if (F->mask[i] == 0) this->acc += fabs((double)F->u[i] - C);
+  __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
+    const uchar4 m = ldmask4(F->mask + i);
+    const V4<T> u = ld4(F->u + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (mask_at(m, q) == 0) this->acc += fabs((double)u.v[q] - C);
   }
 };
 
@@ -259,15 +303,19 @@ template <typename T>
 struct EpiUpdate : EpiBase<T> {
   const Film<T>* F;
   T A, C;
-  __device__ void operator()(int y, int x, const T* in, T* out) {
-    const long long i = (long long)y * F->nx + x;
-    T h = F->hd[i];
-    if (F->mask[i] == 0) {
-      const T w = in[0] - C * F->q2[i];
-      h = (h - A) - w;
-      F->hd[i] = h;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(F->mask + i);
+    V4<T> h = ld4(F->hd + i);
+    const V4<T> q2 = ldg4(F->q2 + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (mask_at(m, q) == 0) {
+        const T w = in[0].v[q] - C * q2.v[q];
+        h.v[q] = (h.v[q] - A) - w;
+      }
+      this->acc += (double)h.v[q];
     }
-    this->acc += (double)h;
+    st4(F->hd + i, h);
     out[0] = h;
   }
 };
@@ -282,18 +330,27 @@ struct EpiFinal : EpiBase<T> {
   bool err;
   double h, rtol, atol;
   const double* k1; const double* k2; const double* k3; const double* y; const double* ynew;
-  __device__ void operator()(int yy, int x, const T*, T*) {
-    const long long i = (long long)yy * F->nx + x;
-    const double g = F->mask[i] != 0 ? (double)F->u[i] - C : 0.0;
-    kout[i] = g;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
+    const uchar4 m = ldmask4(F->mask + i);
+    const V4<T> u = ld4(F->u + i);
+    V4<double> g;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g.v[q] = mask_at(m, q) != 0 ? (double)u.v[q] - C : 0.0;
+    st4(kout + i, g);
     if (err) {
-      const double E = h * (-5.0 / 72.0 * k1[i] + 1.0 / 12.0 * k2[i] + 1.0 / 9.0 * k3[i] - 0.125 * g);
-      const double sc = atol + rtol * fmax(fabs(y[i]), fabs(ynew[i]));
-      double q = fabs(E) / sc;
-      if (!(q == q) || isinf(q)) q = 1e300;                  // non-finite -> rejected step
-      this->accmax = fmax(this->accmax, q);
+      const V4<double> a1 = ld4(k1 + i), a2 = ld4(k2 + i), a3 = ld4(k3 + i), yy = ld4(y + i), yn = ld4(ynew + i);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double E = h * (-5.0 / 72.0 * a1.v[q] + 1.0 / 12.0 * a2.v[q] + 1.0 / 9.0 * a3.v[q] - 0.125 * g.v[q]);
+        const double sc = atol + rtol * fmax(fabs(yy.v[q]), fabs(yn.v[q]));
+        double r = fabs(E) / sc;
+        if (!(r == r) || isinf(r)) r = 1e300;                // non-finite -> rejected step
+        this->accmax = fmax(this->accmax, r);
+      }
     } else {
-      if (!isfinite(g)) this->accmax = 1.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (!isfinite(g.v[q])) this->accmax = 1.0;
     }
   }
 };
@@ -303,8 +360,9 @@ template <typename T>
 struct EpiMoment : EpiBase<T> {
   const Film<T>* F;
   const double* g;
-  __device__ void operator()(int y, int x, const T*, T*) {
-    this->acc += g[(long long)y * F->nx + x];
+  __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
+    const V4<double> v = ld4(g + i);
+    this->acc += (v.v[0] + v.v[1]) + (v.v[2] + v.v[3]);
   }
 };
 
@@ -364,11 +422,21 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     if (!have_out) { C = 0.0; r = 0.0; break; }
     C = F.total(1, F.rb1) / nout;                                       // Eq. 11
     {
+      // P8 (residual, row items) and P9 (K2 column items) share one phase and one item space
       EpiResid<T> e; e.F = &F; e.C = C;
-      F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 2);                       // P8
+      const int n8 = F.ny / F.rb1, n9 = F.nkx;
+      for (int it = F.wq.next(d.gb, &F.sh.item); it < n8 + n9; it = F.wq.next(d.gb, &F.sh.item)) {
+        if (it < n8) {
+          e.acc = 0.0;
+          F.template row_item<0, 0>(it * F.rb1, F.rb1, nullptr, nullptr, e);
+          const double v = block_sum(e.acc, F.sh.red);
+          if (threadIdx.x == 0) d.partials[(size_t)2 * d.max_items + it] = v;
+        } else {
+          F.col_item(it - n8, F.Sb, 1, F.Sb, 1, OP_K2);
+        }
+      }
+      F.wq.end_phase(n8 + n9);
     }
-    // P9 runs in the same phase as P8; its result is discarded when the test stops the loop
-    F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                    // P9
     if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
     r = F.total(2, F.rb1) / nout;
     const bool last = (i == itmax - 1);
@@ -427,6 +495,9 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
     sh.A_prev = st->A_prev;
   }
   __syncthreads();
+  table_to_smem<T>(sm + 2 * BATCH_PAD, (const C2<T>*)d.tw_x, d.nx);
+  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx, (const C2<T>*)d.tw_y, d.ny);
+  __syncthreads();
   Film<T> F(d, sm, sh);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int status = ST_OK;
@@ -477,8 +548,10 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
   }
 }
 
-size_t kernel_smem_bytes(int precision) {
-  return (size_t)2 * BATCH_PAD * (precision ? sizeof(C2<float>) : sizeof(C2<double>));
+size_t kernel_smem_bytes(const Desc& d) {
+  // two FFT buffers, then the twiddle tables of the three axes
+  const size_t c = d.precision ? sizeof(C2<float>) : sizeof(C2<double>);
+  return (2 * (size_t)BATCH_PAD + d.nx + d.ny + d.nz) * c;
 }
 
 int film_max_blocks(int precision, size_t smem) {
@@ -497,7 +570,7 @@ cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaS
   Desc dd = d;
   KernelArgs aa = a;
   void* args[] = {&dd, &aa};
-  const size_t smem = kernel_smem_bytes(precision);
+  const size_t smem = kernel_smem_bytes(d);
   const void* fn = precision ? (const void*)film_kernel<float> : (const void*)film_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);
 }

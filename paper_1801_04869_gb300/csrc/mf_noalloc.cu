@@ -131,7 +131,8 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   d.he_t = (const double*)(w + oknots);
   d.he_v = d.he_t + (p->he_knots > 0 ? p->he_knots : 1);
 
-  const size_t smem = kernel_smem_bytes(precision);
+  d.nz = 1;
+  const size_t smem = kernel_smem_bytes(d);
   const int per_sm = film_max_blocks(precision, smem);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -13,68 +13,101 @@
 
 namespace mf {
 
-// Gather the half spectra of rows [2 pr, 2 pr + 1] of `nin` fields from global memory into
+// Two adjacent complex values (one pair of rows at one x-wavenumber) moved as one vector.
+template <typename T> struct alignas(2 * sizeof(C2<T>)) CPair { C2<T> a, b; };
+
+// Gather the half spectra of rows [2 pr, 2 pr + 1] of NIN fields from global memory into
 // packed complex lines of length nx in shared buffer `sm`, then inverse-transform them along
 // x (second buffer `sm2`).  Returns the buffer holding the rows (row 2pr in .x, 2pr+1 in .y).
-// Global element (f, kx, row r) lives at src + f * fstride + kx * kstride + r.
-template <typename T>
-__device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, const C2<T>* src, long long fstride,
-                                                    long long kstride, int nin, int npair,
-                                                    int lgx, const C2<T>* __restrict__ twx) {
+// Global element (f, kx, row r) lives at src + f * fstride + kx * kstride + r; each thread
+// issues U independent vector loads before it writes shared memory.
+template <typename T, int NIN>
+__device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, const C2<T>* src,
+                                                      long long fstride, long long kstride,
+                                                      int npair, int lgpair, int lgx,
+                                                      const C2<T>* __restrict__ twx) {
+  constexpr int U = 2;
   const int nx = 1 << lgx, half = nx >> 1;
   const int per_f = npair * (half + 1);
-  for (int e = threadIdx.x; e < nin * per_f; e += NT) {
-    const int f = e / per_f;
-    const int rest = e - f * per_f;
-    const int k = rest / npair;
-    const int pr = rest - k * npair;
-    const C2<T>* p = src + f * fstride + (long long)k * kstride + 2 * pr;
-    const C2<T> A = p[0], B = p[1];
-    const int z0 = (f * npair + pr) << lgx;
-    if (k == 0 || k == half) {
-      sm[sp(z0 + k)] = C2<T>{A.x, B.x};
-    } else {
-      sm[sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
-      sm[sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
+  const int total = NIN * per_f;
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * U) {
+    CPair<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) {
+        const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
+        const int rest = e - f * per_f;
+        const int k = rest >> lgpair, pr = rest & (npair - 1);
+        v[u] = *(const CPair<T>*)(src + f * fstride + (long long)k * kstride + 2 * pr);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) {
+        const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
+        const int rest = e - f * per_f;
+        const int k = rest >> lgpair, pr = rest & (npair - 1);
+        const C2<T> A = v[u].a, B = v[u].b;
+        const int z0 = (f * npair + pr) << lgx;
+        if (k == 0 || k == half) {
+          sm[sp(z0 + k)] = C2<T>{A.x, B.x};
+        } else {
+          sm[sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
+          sm[sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
+        }
+      }
     }
   }
   __syncthreads();
-  return fft_lines<T, +1>(sm, sm2, lgx, nin * npair, twx);
+  return fft_lines<T, +1>(sm, sm2, lgx, NIN * npair, twx);
 }
 
-// Forward-transform `nout` fields of packed row pairs (in `sm`, second buffer `sm2`) along x
+// Forward-transform NOUT fields of packed row pairs (in `sm_in`, second buffer `sm2`) along x
 // and scatter their half spectra.
-template <typename T>
-__device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C2<T>* dst, long long fstride,
-                                                     long long kstride, int nout, int npair,
-                                                     int lgx, const C2<T>* __restrict__ twx) {
+template <typename T, int NOUT>
+__device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C2<T>* dst,
+                                                     long long fstride, long long kstride,
+                                                     int npair, int lgpair, int lgx,
+                                                     const C2<T>* __restrict__ twx) {
   const int nx = 1 << lgx, half = nx >> 1;
-  const C2<T>* sm = fft_lines<T, -1>(sm_in, sm2, lgx, nout * npair, twx);
+  const C2<T>* sm = fft_lines<T, -1>(sm_in, sm2, lgx, NOUT * npair, twx);
   const int per_f = npair * (half + 1);
-  for (int e = threadIdx.x; e < nout * per_f; e += NT) {
-    const int f = e / per_f;
+  for (int e = threadIdx.x; e < NOUT * per_f; e += NT) {
+    const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
     const int rest = e - f * per_f;
-    const int k = rest / npair;
-    const int pr = rest - k * npair;
+    const int k = rest >> lgpair, pr = rest & (npair - 1);
     const int z0 = (f * npair + pr) << lgx;
     const C2<T> zk = sm[sp(z0 + k)], zm = sm[sp(z0 + ((nx - k) & (nx - 1)))];
     const T hh = (T)0.5;
-    C2<T> A = {hh * (zk.x + zm.x), hh * (zk.y - zm.y)};
-    C2<T> B = {hh * (zk.y + zm.y), hh * (zm.x - zk.x)};   // -i (zk - conj(zm)) / 2
-    C2<T>* p = dst + f * fstride + (long long)k * kstride + 2 * pr;
-    p[0] = A;
-    p[1] = B;
+    CPair<T> o;
+    o.a = C2<T>{hh * (zk.x + zm.x), hh * (zk.y - zm.y)};
+    o.b = C2<T>{hh * (zk.y + zm.y), hh * (zm.x - zk.x)};   // -i (zk - conj(zm)) / 2
+    *(CPair<T>*)(dst + f * fstride + (long long)k * kstride + 2 * pr) = o;
   }
   __syncthreads();
 }
 
-// Load `n` contiguous lines of length L (line j at src + j * stride) into shared memory.
+// Load `n` contiguous lines of length L (line j at src + j * stride) into shared memory,
+// U loads in flight per thread.
 template <typename T>
 __device__ __forceinline__ void lines_load(C2<T>* sm, const C2<T>* src, long long stride, int n, int lgL) {
+  constexpr int U = 4;
   const int L = 1 << lgL;
-  for (int e = threadIdx.x; e < (n << lgL); e += NT) {
-    const int j = e >> lgL, i = e & (L - 1);
-    sm[sp(e)] = src[j * stride + i];
+  const int total = n << lgL;
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * U) {
+    C2<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) v[u] = src[(e >> lgL) * stride + (e & (L - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) sm[sp(e)] = v[u];
+    }
   }
   __syncthreads();
 }
@@ -86,6 +119,45 @@ __device__ __forceinline__ void lines_store(const C2<T>* sm, C2<T>* dst, long lo
     dst[j * stride + i] = sm[sp(e)];
   }
   __syncthreads();
+}
+
+// Copy `n` complex values of a global table into shared memory (start of a launch).
+template <typename T>
+__device__ __forceinline__ void table_to_smem(C2<T>* dst, const C2<T>* __restrict__ src, int n) {
+  for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
+}
+
+// ------------------------------------------------------------------------------------------
+// four consecutive cells: vector loads and stores (index a multiple of 4, 16-byte aligned)
+// ------------------------------------------------------------------------------------------
+template <typename T> struct V4 { T v[4]; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 a = *(const float4*)p;
+  return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 a = ((const double2*)p)[0], b = ((const double2*)p)[1];
+  return {{a.x, a.y, b.x, b.y}};
+}
+// read-only for the whole launch (non-coherent path)
+__device__ __forceinline__ V4<float> ldg4(const float* p) {
+  const float4 a = __ldg((const float4*)p);
+  return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ldg4(const double* p) {
+  const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& v) {
+  *(float4*)p = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& v) {
+  ((double2*)p)[0] = make_double2(v.v[0], v.v[1]);
+  ((double2*)p)[1] = make_double2(v.v[2], v.v[3]);
+}
+__device__ __forceinline__ uchar4 ldmask4(const uint8_t* p) { return __ldg((const uchar4*)p); }
+__device__ __forceinline__ int mask_at(const uchar4& m, int j) {
+  return j == 0 ? m.x : (j == 1 ? m.y : (j == 2 ? m.z : m.w));
 }
 
 __device__ __forceinline__ float powt(float a, float b) { return powf(a, b); }

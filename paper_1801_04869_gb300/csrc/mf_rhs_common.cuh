@@ -19,6 +19,7 @@ struct StageIn {
 // per-CTA copy of the scalars every CTA agrees on
 struct Shared {
   double red[NT / 32];
+  int item;                      // broadcast slot of the dynamic schedule
   double A, C, r, hed;
   int warm_valid;
   double A_prev;
