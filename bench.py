@@ -153,6 +153,63 @@ def cpu_sample(wl, iters: int, budget_s: float):
     return n / el, n, el
 
 
+def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128):
+    """Secondary line: the 3D cube (n_grid/2 cells per side in n_grid^3), FP32 transforms."""
+    wl = W.cube_bulk(n_grid, precision=1)
+    p = native.from_workload(wl)
+    p.mf_set_state(0.0, None, h=1e-3)
+    p.mf_advance(1.0, max_attempts=warmup)
+    torch.cuda.synchronize()
+    i0 = p.mf_get_info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(p.stream)
+    p.mf_advance(1.0, max_attempts=steps)
+    e1.record(p.stream)
+    torch.cuda.synchronize()
+    i1 = p.mf_get_info()
+    sec = e0.elapsed_time(e1) / 1000.0
+    n_rhs, n_it = i1["n_rhs"] - i0["n_rhs"], i1["n_iters"] - i0["n_iters"]
+    M3 = float(n_grid) ** 3 * 4.0
+    alg = (60.0 * n_rhs + 60.0 * n_it) * M3
+    peak, kind = hbm_peak()
+    return {"workload": wl.name, "value": n_rhs / sec, "unit": UNIT, "steps": i1["n_attempts"] - i0["n_attempts"],
+            "mean_outside_iterations": n_it / max(n_rhs, 1),
+            "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
+                         "bytes_model": f"(60 + 60 I) M3 per RHS, M3 = {n_grid}^3 x 4 B"}}
+
+
+def full_ramp_leg(native, W, torch, precision: int):
+    """Full ramp of the square film (64^2 cells in 128^2, n = 19, h_e 0 -> 0.5 over [0, 1]) on
+    the GPU, timed end to end, with its error against the free-running FP64 oracle."""
+    import numpy as np
+    from oracle.bs23 import BS23
+    from oracle.waveform import Waveform
+    wl = W.square_film_128(precision=precision)
+    p = native.from_workload(wl)
+    t_out = np.linspace(0.1, 1.0, 10)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    m, hz = p.mf_run_ramp(t_out, want_fields=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - w0
+    info = p.mf_get_info()
+    o = _oracle_problem(wl)
+    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol)
+    s.start(0.0, np.zeros((wl.ny, wl.nx)), 1.0)
+    c0 = time.perf_counter()
+    s.advance(1.0)
+    cpu_sec = time.perf_counter() - c0
+    hz_ref = o.hz(1.0, s.y)
+    hz_gpu = hz[-1].cpu().numpy().reshape(wl.ny, wl.nx)
+    return {"workload": wl.name, "transforms": "f32" if precision else "f64", "seconds": sec,
+            "accepted_steps": info["n_accepted"], "rejected_steps": info["n_rejected"],
+            "rhs_evals": info["n_rhs"],
+            "rel_err_hz": float(np.linalg.norm(hz_gpu - hz_ref) / np.linalg.norm(hz_ref)),
+            "rel_err_m": float(abs(m[-1, 0] - o.magnetization(s.y)) / abs(o.magnetization(s.y))),
+            "oracle_seconds": cpu_sec}
+
+
 def cores_used() -> int:
     # numpy's FFT (pocketfft) and elementwise kernels run on one thread
     return 1
@@ -183,6 +240,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the bulk and full-ramp legs")
     ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
     args = ap.parse_args()
 
@@ -295,6 +353,8 @@ def main():
                              f"{max(1, round(mean_it))} forced outside iterations each "
                              f"({el:.1f} s on the host)"}
         info = p.mf_get_info()
+        bulk = bulk_leg(native, W, torch) if not args.no_extra else None
+        ramps = [full_ramp_leg(native, W, torch, prec) for prec in (0, 1)] if not args.no_extra else None
         line = {
             "metric": METRIC, "value": rhs_all / sec_all, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec_all / args.steps,
@@ -318,6 +378,8 @@ def main():
                     "d2h_bytes_per_step": ncell * 8 + 8},
             "gpu_launches": 1,
             "clocks": ck.summary(),
+            "bulk": bulk,
+            "full_ramp": ramps,
         }
         print(json.dumps(line))
     if dist:

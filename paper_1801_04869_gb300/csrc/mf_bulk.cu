@@ -98,7 +98,7 @@ struct Bulk {
   __device__ void xpass(Epi& epi, int slot) {
     const int per_z = ny / rb;
     const int nitems = per_z * nz;
-    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
@@ -107,7 +107,7 @@ struct Bulk {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
-    wq.end_phase(nitems);
+    wq.end_phase();
   }
   __device__ double total(int slot, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, (ny / rb) * nz, is_max, sh.red);
@@ -117,15 +117,16 @@ struct Bulk {
   __device__ void yfwd() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
-      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
-        const int l = e >> lgy, y = e & (ny - 1);
-        const int c = l / zs, dz = l - c * zs;
-        sm[sp(e)] = S1[c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y];
-      }
-      __syncthreads();
+      gather_batched<T, 4>(sm, S1, nl << lgy,
+          [&](int e) {
+            const int l = e >> lgy, y = e & (ny - 1);
+            const int c = l / zs, dz = l - c * zs;
+            return c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y;
+          },
+          [](int e) { return e; });
       const C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nl, twy);
       for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
         const int dz = e % zs, rest = e / zs;
@@ -134,21 +135,26 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase(nitems);
+    wq.end_phase();
   }
   // ---- y pass, inverse: S2 -> S1 ----
   __device__ void yinv() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
-      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
-        const int dz = e % zs, rest = e / zs;
-        const int ky = rest & (ny - 1), c = rest >> lgy;
-        sm[sp(((c * zs + dz) << lgy) + ky)] = S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz];
-      }
-      __syncthreads();
+      gather_batched<T, 4>(sm, S2, nl << lgy,
+          [&](int e) {
+            const int dz = e % zs, rest = e / zs;
+            const int ky = rest & (ny - 1), c = rest >> lgy;
+            return c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz;
+          },
+          [&](int e) {
+            const int dz = e % zs, rest = e / zs;
+            const int ky = rest & (ny - 1), c = rest >> lgy;
+            return ((c * zs + dz) << lgy) + ky;
+          });
       const C2<T>* X = fft_lines<T, +1>(sm, sm2, lgy, nl, twy);
       for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
         const int l = e >> lgy, y = e & (ny - 1);
@@ -157,22 +163,20 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase(nitems);
+    wq.end_phase();
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
   __device__ void zpass(int op) {
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
-    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
       const int kx = it / per_kx, ky0 = (it % per_kx) * P;
       const long long base = ((long long)kx * ny + ky0) * nz;
       const int pl = P << lgz;                       // values per component
-      for (int e = threadIdx.x; e < 3 * pl; e += NT) {
-        const int c = e / pl, r = e - c * pl;
-        sm[sp(e)] = S2[c * nspec + base + r];
-      }
-      __syncthreads();
+      gather_batched<T, 4>(sm, S2, 3 * pl,
+          [&](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
+          [](int e) { return e; });
       C2<T>* X = fft_lines<T, -1>(sm, sm2, lgz, 3 * P, twz);
       C2<T>* Y = X == sm ? sm2 : sm;
       const T kxv = ktab[kx], gx = gtab[kx];
@@ -208,7 +212,7 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase(nitems);
+    wq.end_phase();
   }
 
   // Yf, Z(op), Yi with barriers; the x passes before and after are separate

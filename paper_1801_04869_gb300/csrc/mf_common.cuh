@@ -73,25 +73,35 @@ struct GridBarrier {
   unsigned long long work;       // work-item counter of the dynamic schedule (monotonic)
 };
 
-// Dynamic schedule of the work items of one phase: CTAs take items from a monotonic counter.
-// Every CTA ends a phase with exactly one failed grab, so after a phase of n items the counter
-// has advanced by n + gridDim.x in every CTA's view; `base` tracks that without a reset.
+// Dynamic schedule of the work items of one phase.  CTA b first takes item b (no atomic);
+// when a phase has more items than CTAs, the rest come from a monotonic counter, item =
+// grid + counter - base, and every CTA ends with exactly one failed grab, so the counter
+// advances by (n - grid) + grid in every CTA's view; `base` tracks that without a reset.
+// Phases that use the schedule must be separated by a grid barrier.
 struct WorkQueue {
   unsigned long long base;
-  // next item of the current phase (>= nitems: the phase is done for this CTA).  Phases that
-  // use the schedule must be separated by a grid barrier; a negative index would mean a CTA
-  // grabbed ahead of the others, which raises the abort flag instead of touching memory.
+  int nitems, first;
+  __device__ __forceinline__ int begin(int n) {
+    nitems = n;
+    first = 1;
+    return (int)blockIdx.x < n ? (int)blockIdx.x : n;
+  }
+  // next item after the current one (>= nitems: done).  A negative counter value would mean
+  // a CTA grabbed ahead of the others; it raises the abort flag instead of touching memory.
   __device__ __forceinline__ int next(GridBarrier* gb, int* s_item) {
+    if (nitems <= (int)gridDim.x) return nitems;
     __syncthreads();
     if (threadIdx.x == 0) {
-      long long v = (long long)(atomicAdd(&gb->work, 1ull) - base);
-      if (v < 0) { atomicExch(&gb->abort, 1); v = 0x7fffffff; }
+      long long v = (long long)(atomicAdd(&gb->work, 1ull) - base) + gridDim.x;
+      if (v < (long long)gridDim.x) { atomicExch(&gb->abort, 1); v = 0x7fffffff; }
       *s_item = v > 0x7fffffff ? 0x7fffffff : (int)v;
     }
     __syncthreads();
     return *s_item;
   }
-  __device__ __forceinline__ void end_phase(int nitems) { base += (unsigned long long)nitems + gridDim.x; }
+  __device__ __forceinline__ void end_phase() {
+    if (nitems > (int)gridDim.x) base += (unsigned long long)nitems;   // (n - grid) + grid
+  }
 };
 
 // ------------------------------------------------------------------------------------------

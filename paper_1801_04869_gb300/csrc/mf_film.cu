@@ -65,28 +65,37 @@ struct Film {
 
   __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
 
-  // ---- y pass: forward, multiplier, inverse on x-wavenumber line kx ----
-  __device__ void col_item(int kx, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
-    lines_load<T>(sm, Sin + (long long)kx * ny, nspec, nin, lgy);
-    C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nin, twy);
+  // ---- y pass: forward, multiplier, inverse on nl consecutive x-wavenumber lines ----
+  // shared line f * nl + l holds field f of line kx0 + l
+  __device__ void col_item(int kx0, int nl, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
+    gather_batched<T, 4>(sm, Sin, (nin * nl) << lgy,
+        [&](int e) {
+          const int j = e >> lgy, f = j / nl, l = j - f * nl;
+          return f * nspec + (long long)(kx0 + l) * ny + (e & (ny - 1));
+        },
+        [](int e) { return e; });
+    C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nin * nl, twy);
     C2<T>* Y = X == sm ? sm2 : sm;
     const T s = (T)1 / (T)ncell;
-    const T kxv = ktab[kx], gx = gtab[kx];
-    const T kxo = (kx == half) ? (T)0 : kxv;
-    for (int ky = threadIdx.x; ky < ny; ky += NT) {
-      const T kyv = ktab[nkx + ky], G = gx * gtab[nkx + ky];
+    for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+      const int l = e >> lgy, ky = e & (ny - 1);
+      const int kx = kx0 + l;
+      const T kxv = __ldg(&ktab[kx]), gx = __ldg(&gtab[kx]);
+      const T kxo = (kx == half) ? (T)0 : kxv;
+      const T kyv = __ldg(&ktab[nkx + ky]), G = gx * __ldg(&gtab[nkx + ky]);
       const T kyo = (ky == ny / 2) ? (T)0 : kyv;
       const T k2 = kxv * kxv + kyv * kyv;
-      C2<T> a = X[sp(ky)];
+      const int i0 = (0 * nl + l) * ny + ky, i1 = (1 * nl + l) * ny + ky;
+      C2<T> a = X[sp(i0)];
       if (op == OP_GRAD) {
         const T fx = kxo * G * s, fy = kyo * G * s;
-        X[sp(ky)] = cmul_si(cscale(a, fx), 1);
-        X[sp(ny + ky)] = cmul_si(cscale(a, fy), 1);
+        X[sp(i0)] = cmul_si(cscale(a, fx), 1);
+        X[sp(i1)] = cmul_si(cscale(a, fy), 1);
       } else if (op == OP_CURLNEG) {
-        const C2<T> b = X[sp(ny + ky)];
+        const C2<T> b = X[sp(i1)];
         // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
         C2<T> c = {kyo * a.x - kxo * b.x, kyo * a.y - kxo * b.y};
-        X[sp(ky)] = cmul_si(cscale(c, G * s), 1);
+        X[sp(i0)] = cmul_si(cscale(c, G * s), 1);
       } else {
         T m;
         const T kabs = sqrt(k2);
@@ -94,18 +103,32 @@ struct Film {
         else if (op == OP_K2) m = (T)d.lam * kabs * (T)0.5 * G;
         else if (op == OP_KH) m = kabs * (T)0.5;
         else m = (T)1;
-        X[sp(ky)] = cscale(a, m * s);
+        X[sp(i0)] = cscale(a, m * s);
       }
     }
     __syncthreads();
-    const C2<T>* Z = fft_lines<T, +1>(X, Y, lgy, nout, twy);
-    lines_store<T>(Z, Sout + (long long)kx * ny, nspec, nout, lgy);
+    const C2<T>* Z = fft_lines<T, +1>(X, Y, lgy, nout * nl, twy);
+    for (int e = threadIdx.x; e < ((nout * nl) << lgy); e += NT) {
+      const int j = e >> lgy, f = j / nl, l = j - f * nl;
+      Sout[f * nspec + (long long)(kx0 + l) * ny + (e & (ny - 1))] = Z[sp(e)];
+    }
+    __syncthreads();
+  }
+
+  // lines per column item: fill the shared batch (two lines for single-field operators)
+  __device__ int col_lines(int nf) const {
+    int nl = BATCH / (nf * ny);
+    return nl < 1 ? 1 : (nl > 2 ? 2 : nl);
   }
 
   __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
-    for (int kx = wq.next(d.gb, &sh.item); kx < nkx; kx = wq.next(d.gb, &sh.item))
-      col_item(kx, Sin, nin, Sout, nout, op);
-    wq.end_phase(nkx);
+    const int nl = col_lines(nin > nout ? nin : nout);
+    const int nitems = (nkx + nl - 1) / nl;
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+      const int kx0 = it * nl;
+      col_item(kx0, kx0 + nl <= nkx ? nl : nkx - kx0, Sin, nin, Sout, nout, op);
+    }
+    wq.end_phase();
   }
 
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
@@ -149,7 +172,7 @@ struct Film {
   template <int NIN, int NOUT, class Epi>
   __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
     const int nitems = ny / rb;
-    for (int it = wq.next(d.gb, &sh.item); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
@@ -158,7 +181,7 @@ struct Film {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
-    wq.end_phase(nitems);
+    wq.end_phase();
   }
   __device__ double total(int slot, int rb, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, ny / rb, is_max, sh.red);
@@ -424,18 +447,20 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     {
       // P8 (residual, row items) and P9 (K2 column items) share one phase and one item space
       EpiResid<T> e; e.F = &F; e.C = C;
-      const int n8 = F.ny / F.rb1, n9 = F.nkx;
-      for (int it = F.wq.next(d.gb, &F.sh.item); it < n8 + n9; it = F.wq.next(d.gb, &F.sh.item)) {
+      const int nl9 = F.col_lines(1);
+      const int n8 = F.ny / F.rb1, n9 = (F.nkx + nl9 - 1) / nl9;
+      for (int it = F.wq.begin(n8 + n9); it < n8 + n9; it = F.wq.next(d.gb, &F.sh.item)) {
         if (it < n8) {
           e.acc = 0.0;
           F.template row_item<0, 0>(it * F.rb1, F.rb1, nullptr, nullptr, e);
           const double v = block_sum(e.acc, F.sh.red);
           if (threadIdx.x == 0) d.partials[(size_t)2 * d.max_items + it] = v;
         } else {
-          F.col_item(it - n8, F.Sb, 1, F.Sb, 1, OP_K2);
+          const int kx0 = (it - n8) * nl9;
+          F.col_item(kx0, kx0 + nl9 <= F.nkx ? nl9 : F.nkx - kx0, F.Sb, 1, F.Sb, 1, OP_K2);
         }
       }
-      F.wq.end_phase(n8 + n9);
+      F.wq.end_phase();
     }
     if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
     r = F.total(2, F.rb1) / nout;

@@ -121,6 +121,26 @@ __device__ __forceinline__ void lines_store(const C2<T>* sm, C2<T>* dst, long lo
   __syncthreads();
 }
 
+// Gather `total` complex values into shared memory, value e from src[goff(e)] to
+// sm[sp(soff(e))], with U loads in flight per thread; synchronises at the end.
+template <typename T, int U, class GOff, class SOff>
+__device__ __forceinline__ void gather_batched(C2<T>* sm, const C2<T>* src, int total, GOff goff, SOff soff) {
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * U) {
+    C2<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) v[u] = src[goff(e)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) sm[sp(soff(e))] = v[u];
+    }
+  }
+  __syncthreads();
+}
+
 // Copy `n` complex values of a global table into shared memory (start of a launch).
 template <typename T>
 __device__ __forceinline__ void table_to_smem(C2<T>* dst, const C2<T>* __restrict__ src, int n) {
