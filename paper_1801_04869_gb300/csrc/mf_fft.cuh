@@ -153,4 +153,176 @@ __device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines
   return in;
 }
 
+// ------------------------------------------------------------------------------------------
+// Transform with fused global I/O and a fused spectral multiplier.
+//
+// Forward plan: radices r_0 .. r_{m-1} (the same rule as fft_lines), inverse plan: the reverse
+// order.  The forward last stage (p = L / r_{m-1}) leaves every butterfly's outputs at the
+// natural positions i + j L/r, which are exactly the inputs of the inverse first stage (p = 1,
+// same radix).  So one pass does: forward last stage, multiplier, inverse first stage, all in
+// registers.  The first forward stage reads global memory and the last inverse stage writes
+// global memory directly (both in natural order, coalesced), so the round trip costs m + 1
+// shared-memory exchanges instead of 2m + 3.
+// ------------------------------------------------------------------------------------------
+struct FftPlan {
+  int m;
+  int lgr[8];
+};
+template <typename T>
+__device__ __forceinline__ FftPlan fft_plan(int lgL) {
+  FftPlan P;
+  P.m = 0;
+  int rem = lgL;
+  while (rem > 0) {
+    int l;
+    if (sizeof(T) == 4 && rem >= 4 && rem != 5) l = 4;
+    else if (rem >= 3) l = 3;
+    else l = rem;
+    P.lgr[P.m++] = l;
+    rem -= l;
+  }
+  return P;
+}
+
+// one stage with arbitrary element I/O: ld(line, pos) -> C2<T>, st(line, pos, value)
+template <typename T, int R, int LGR, int DIR, class Ld, class St>
+__device__ __forceinline__ void fft_stage_io(int lgL, int lgp, int nlines, const C2<T>* __restrict__ tw,
+                                             Ld ld, St st) {
+  const int lgq = lgL - LGR;
+  const int q = 1 << lgq;
+  const int p = 1 << lgp;
+  const int nb = nlines << lgq;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int line = b >> lgq, i = b & (q - 1);
+    const int k = i & (p - 1);
+    C2<T> v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = ld(line, i + (j << lgq));
+    if (lgp > 0) {
+      const int step = k << (lgL - lgp - LGR);
+#pragma unroll
+      for (int j = 1; j < R; ++j) {
+        C2<T> w = tw[j * step];
+        if (DIR > 0) w.y = -w.y;
+        v[j] = cmul(v[j], w);
+      }
+    }
+    dft<T, R, DIR>(v);
+    const int dpos = ((i - k) << LGR) + k;
+#pragma unroll
+    for (int j = 0; j < R; ++j) st(line, dpos + (j << lgp), v[j]);
+  }
+  __syncthreads();
+}
+
+template <typename T, int DIR, class Ld, class St>
+__device__ __forceinline__ void fft_stage_io_any(int lgr, int lgL, int lgp, int nlines,
+                                                 const C2<T>* __restrict__ tw, Ld ld, St st) {
+  if constexpr (sizeof(T) == 4) {
+    if (lgr == 4) { fft_stage_io<T, 16, 4, DIR>(lgL, lgp, nlines, tw, ld, st); return; }
+  }
+  if (lgr == 3) fft_stage_io<T, 8, 3, DIR>(lgL, lgp, nlines, tw, ld, st);
+  else if (lgr == 2) fft_stage_io<T, 4, 2, DIR>(lgL, lgp, nlines, tw, ld, st);
+  else fft_stage_io<T, 2, 1, DIR>(lgL, lgp, nlines, tw, ld, st);
+}
+
+// the fused middle pass: forward last stage (radix R) on NFI input fields, mul(l, pos, x[], y[])
+// per position, inverse first stage on NFO output fields.  Shared line f * nl + l holds field
+// f of line group l.
+template <typename T, int R, int LGR, int NFI, int NFO, class Mul>
+__device__ __forceinline__ void fft_middle(const C2<T>* in, C2<T>* out, int lgL, int nl,
+                                           const C2<T>* __restrict__ tw, Mul mul) {
+  const int lgq = lgL - LGR;
+  const int q = 1 << lgq;
+  const int nb = nl << lgq;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int l = b >> lgq, i = b & (q - 1);
+    C2<T> x[NFI][R];
+#pragma unroll
+    for (int f = 0; f < NFI; ++f) {
+      const int base = ((f * nl + l) << lgL) + i;
+#pragma unroll
+      for (int j = 0; j < R; ++j) x[f][j] = in[sp(base + (j << lgq))];
+      // twiddles of the last forward stage: p = q, k = i, w^(j i) with w = exp(-2 pi i / L)
+#pragma unroll
+      for (int j = 1; j < R; ++j) x[f][j] = cmul(x[f][j], tw[j * i]);
+      dft<T, R, -1>(x[f]);
+    }
+    C2<T> y[NFO][R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      C2<T> xi[NFI], yo[NFO];
+#pragma unroll
+      for (int f = 0; f < NFI; ++f) xi[f] = x[f][j];
+      mul(l, i + (j << lgq), xi, yo);
+#pragma unroll
+      for (int g = 0; g < NFO; ++g) y[g][j] = yo[g];
+    }
+#pragma unroll
+    for (int g = 0; g < NFO; ++g) {
+      dft<T, R, +1>(y[g]);
+      const int base = ((g * nl + l) << lgL) + (i << LGR);
+#pragma unroll
+      for (int j = 0; j < R; ++j) out[sp(base + j)] = y[g][j];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int NFI, int NFO, class Mul>
+__device__ __forceinline__ void fft_middle_any(int lgr, const C2<T>* in, C2<T>* out, int lgL, int nl,
+                                               const C2<T>* __restrict__ tw, Mul mul) {
+  if constexpr (sizeof(T) == 4) {
+    if (lgr == 4) { fft_middle<T, 16, 4, NFI, NFO>(in, out, lgL, nl, tw, mul); return; }
+  }
+  if (lgr == 3) fft_middle<T, 8, 3, NFI, NFO>(in, out, lgL, nl, tw, mul);
+  else if (lgr == 2) fft_middle<T, 4, 2, NFI, NFO>(in, out, lgL, nl, tw, mul);
+  else fft_middle<T, 2, 1, NFI, NFO>(in, out, lgL, nl, tw, mul);
+}
+
+// Round trip F^-1[M F(.)] of NFI -> NFO fields on nl line groups, global in and out:
+// gsrc(f, l) / gdst(g, l) give the first element of field f / g of group l (contiguous lines).
+// Needs a plan of at least two stages.
+template <typename T, int NFI, int NFO, class Src, class Dst, class Mul>
+__device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T>* __restrict__ tw,
+                               Src gsrc, Dst gdst, Mul mul) {
+  const FftPlan P = fft_plan<T>(lgL);
+  const int L = 1 << lgL;
+  int lgp = 0;
+  // forward stage 0: global -> sa
+  fft_stage_io_any<T, -1>(P.lgr[0], lgL, 0, NFI * nl, tw,
+      [&](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
+      [&](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
+  lgp += P.lgr[0];
+  C2<T>* cur = sa;
+  C2<T>* oth = sb;
+  for (int s = 1; s < P.m - 1; ++s) {
+    const int lgr = P.lgr[s];
+    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
+    else if (lgr == 3) fft_stage<T, 8, 3, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
+    else if (lgr == 2) fft_stage<T, 4, 2, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
+    else fft_stage<T, 2, 1, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
+    lgp += lgr;
+    C2<T>* t = cur; cur = oth; oth = t;
+  }
+  // forward last stage + multiplier + inverse first stage
+  fft_middle_any<T, NFI, NFO>(P.lgr[P.m - 1], cur, oth, lgL, nl, tw, mul);
+  { C2<T>* t = cur; cur = oth; oth = t; }
+  int lgpi = P.lgr[P.m - 1];
+  for (int s = P.m - 2; s >= 1; --s) {
+    const int lgr = P.lgr[s];
+    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
+    else if (lgr == 3) fft_stage<T, 8, 3, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
+    else if (lgr == 2) fft_stage<T, 4, 2, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
+    else fft_stage<T, 2, 1, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
+    lgpi += lgr;
+    C2<T>* t = cur; cur = oth; oth = t;
+  }
+  // inverse last stage: shared -> global
+  fft_stage_io_any<T, +1>(P.lgr[0], lgL, lgpi, NFO * nl, tw,
+      [&](int line, int pos) { return cur[sp((line << lgL) + pos)]; },
+      [&](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
+  (void)L;
+}
+
 }  // namespace mf

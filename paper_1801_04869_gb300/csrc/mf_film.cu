@@ -68,6 +68,50 @@ struct Film {
   // ---- y pass: forward, multiplier, inverse on nl consecutive x-wavenumber lines ----
   // shared line f * nl + l holds field f of line kx0 + l
   __device__ void col_item(int kx0, int nl, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
+    if (fft_plan<T>(lgy).m >= 2) {
+      // fused round trip: global -> first stage, multiplier between the forward last and the
+      // inverse first stage, last stage -> global
+      auto src = [&](int f, int l) { return Sin + f * nspec + (long long)(kx0 + l) * ny; };
+      auto dst = [&](int g, int l) { return Sout + g * nspec + (long long)(kx0 + l) * ny; };
+      const T s = (T)1 / (T)ncell;
+      auto coef = [&](int l, int ky, T& kxo, T& kyo, T& k2, T& G) {
+        const int kx = kx0 + l;
+        const T kxv = __ldg(&ktab[kx]), kyv = __ldg(&ktab[nkx + ky]);
+        kxo = (kx == half) ? (T)0 : kxv;
+        kyo = (ky == ny / 2) ? (T)0 : kyv;
+        k2 = kxv * kxv + kyv * kyv;
+        G = __ldg(&gtab[kx]) * __ldg(&gtab[nkx + ky]);
+      };
+      if (op == OP_GRAD) {
+        fft_round_trip<T, 1, 2>(sm, sm2, lgy, nl, twy, src, dst,
+            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+              T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
+              y[0] = cmul_si(cscale(x[0], kxo * G * s), 1);
+              y[1] = cmul_si(cscale(x[0], kyo * G * s), 1);
+            });
+      } else if (op == OP_CURLNEG) {
+        fft_round_trip<T, 2, 1>(sm, sm2, lgy, nl, twy, src, dst,
+            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+              T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
+              // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
+              const C2<T> c = {kyo * x[0].x - kxo * x[1].x, kyo * x[0].y - kxo * x[1].y};
+              y[0] = cmul_si(cscale(c, G * s), 1);
+            });
+      } else {
+        fft_round_trip<T, 1, 1>(sm, sm2, lgy, nl, twy, src, dst,
+            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+              T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
+              const T kabs = sqrt(k2);
+              T m;
+              if (op == OP_K1) m = (k2 > (T)0) ? (T)2 / kabs : (T)0;
+              else if (op == OP_K2) m = (T)d.lam * kabs * (T)0.5 * G;
+              else if (op == OP_KH) m = kabs * (T)0.5;
+              else m = (T)1;
+              y[0] = cscale(x[0], m * s);
+            });
+      }
+      return;
+    }
     gather_batched<T, 4>(sm, Sin, (nin * nl) << lgy,
         [&](int e) {
           const int j = e >> lgy, f = j / nl, l = j - f * nl;
