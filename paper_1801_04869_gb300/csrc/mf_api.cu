@@ -8,6 +8,7 @@
 
 #include "../../include/mf.h"
 #include "mf_common.cuh"
+#include "mf_tables.h"
 
 using namespace mf;
 
@@ -83,9 +84,9 @@ Layout layout(const mf_params* p) {
   L.q2 = take(p->dim == 2 ? L.ncell * ts : 0);
   L.jc = take(p->jc_map ? L.ncell * ts : 0);
   L.mask = take(L.ncell);
-  L.twx = take(p->nx * 2 * ts);
-  L.twy = take(p->ny * 2 * ts);
-  L.twz = take(nz * 2 * ts);
+  L.twx = take(2 * p->nx * 2 * ts);             // stage-ordered tables A and B (< 2 L entries)
+  L.twy = take(2 * p->ny * 2 * ts);
+  L.twz = take(2 * nz * 2 * ts);
   const int nk = p->nx / 2 + 1 + p->ny + nz;
   L.ktab = take(nk * ts);
   L.gtab = take(nk * ts);
@@ -105,13 +106,13 @@ void fill_tables(const mf_params* p, double sigma, std::vector<char>& tw, std::v
                  std::vector<char>& gt) {
   const int nz = p->dim == 2 ? 1 : p->nz;
   const int ns[3] = {p->nx, p->ny, nz};
+  // per axis: stage-ordered twiddle tables, each block padded to 2 L complex entries
   std::vector<T> t;
-  for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < ns[a]; ++j) {
-      const double ang = -2.0 * M_PI * (double)j / (double)ns[a];
-      t.push_back((T)std::cos(ang));
-      t.push_back((T)std::sin(ang));
-    }
+  for (int a = 0; a < 3; ++a) {
+    std::vector<T> blk(4 * (size_t)ns[a], (T)0);
+    stage_twiddles<T>(ns[a], blk.data());
+    t.insert(t.end(), blk.begin(), blk.end());
+  }
   tw.assign((const char*)t.data(), (const char*)(t.data() + t.size()));
   std::vector<T> k, g;
   const double Ls[3] = {p->Lx, p->Ly, p->dim == 2 ? 1.0 : p->Lz};
@@ -320,7 +321,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   };
   cp(w + L.mask, p->mask, L.ncell);
   if (p->jc_map) cp(w + L.jc, jcbuf.data(), jcbuf.size());
-  const size_t twx = p->nx * 2 * ts, twy = p->ny * 2 * ts, twz = nz * 2 * ts;
+  const size_t twx = 2 * p->nx * 2 * ts, twy = 2 * p->ny * 2 * ts, twz = 2 * nz * 2 * ts;
   cp(w + L.twx, tw.data(), twx);
   cp(w + L.twy, tw.data() + twx, twy);
   cp(w + L.twz, tw.data() + twx + twy, twz);

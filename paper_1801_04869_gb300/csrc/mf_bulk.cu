@@ -50,9 +50,9 @@ struct Bulk {
     S1 = (C2<T>*)d.Sa; S2 = (C2<T>*)d.Sb;
     hd = (T*)d.hd;
     mask = d.mask; jcmap = (const T*)d.jcmap;
-    twx = sm + 2 * BATCH_PAD;                   // twiddle tables copied to shared memory
-    twy = twx + nx;
-    twz = twy + ny;
+    twx = (const C2<T>*)d.tw_x;
+    twy = (const C2<T>*)d.tw_y;
+    twz = (const C2<T>*)d.tw_z;
     ktab = (const T*)d.ktab; gtab = (const T*)d.gtab;
     rb = d.rows_per_item;
     zs = d.zs_per_item;
@@ -69,7 +69,7 @@ struct Bulk {
 
   // ---- x pass over rows (z, y0 .. y0 + rb): inverse of NIN = 0|3 fields, epilogue, forward ----
   template <int NIN, int NOUT, class Epi>
-  __device__ void xitem(int z, int y0, Epi& epi) {
+  __device__ __noinline__ void xitem(int z, int y0, Epi& epi) {
     const int npair = rb / 2;
     const long long off = (long long)z * nkx * ny + y0;
     C2<T>* X = sm;
@@ -114,7 +114,7 @@ struct Bulk {
   }
 
   // ---- y pass, forward: S1[c][z][kx][:] -> S2[c][kx][:][z] for z in [z0, z0 + zs) ----
-  __device__ void yfwd() {
+  __device__ __noinline__ void yfwd() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
     for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
@@ -138,7 +138,7 @@ struct Bulk {
     wq.end_phase();
   }
   // ---- y pass, inverse: S2 -> S1 ----
-  __device__ void yinv() {
+  __device__ __noinline__ void yinv() {
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
     for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
@@ -166,7 +166,7 @@ struct Bulk {
     wq.end_phase();
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
-  __device__ void zpass(int op) {
+  __device__ __noinline__ void zpass(int op) {
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
@@ -454,10 +454,6 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
     sh.warm_valid = st->warm_valid;
     sh.A_prev = 0.0;
   }
-  __syncthreads();
-  table_to_smem<T>(sm + 2 * BATCH_PAD, (const C2<T>*)d.tw_x, d.nx);
-  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx, (const C2<T>*)d.tw_y, d.ny);
-  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx + d.ny, (const C2<T>*)d.tw_z, d.nz);
   __syncthreads();
   Bulk<T> B(d, sm, sh);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;

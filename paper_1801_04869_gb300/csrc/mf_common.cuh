@@ -20,7 +20,8 @@ constexpr int BATCH_PAD = BATCH + BATCH / 16;
 // ------------------------------------------------------------------------------------------
 // complex numbers
 // ------------------------------------------------------------------------------------------
-template <typename T> struct C2 { T x, y; };
+// 8-byte (float) or 16-byte (double) alignment so that a complex value moves as one vector access
+template <typename T> struct alignas(2 * sizeof(T)) C2 { T x, y; };
 template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
 template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
@@ -31,6 +32,16 @@ template <typename T> __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { re
 // a * (s i) for s = +-1
 template <typename T> __device__ __forceinline__ C2<T> cmul_si(C2<T> a, int s) {
   return s > 0 ? C2<T>{-a.y, a.x} : C2<T>{a.y, -a.x};
+}
+
+// read-only (non-coherent) load of a complex value
+__device__ __forceinline__ C2<float> ldg_c2(const C2<float>* p) {
+  const float2 v = __ldg((const float2*)p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ C2<double> ldg_c2(const C2<double>* p) {
+  const double2 v = __ldg((const double2*)p);
+  return {v.x, v.y};
 }
 
 // ------------------------------------------------------------------------------------------
@@ -65,12 +76,17 @@ struct SolverState {
   double pad[4];
 };
 
-struct GridBarrier {
+// The arrival counter, the generation word that waiting CTAs poll, and the work counter of the
+// dynamic schedule sit on separate 128-byte lines so that polling does not slow the atomics.
+struct alignas(128) GridBarrier {
   unsigned int count;
-  unsigned int gen;
   int abort;
   int where;
+  unsigned int pad0[29];
+  unsigned int gen;
+  unsigned int pad1[31];
   unsigned long long work;       // work-item counter of the dynamic schedule (monotonic)
+  unsigned long long pad2[15];
 };
 
 // Dynamic schedule of the work items of one phase.  CTA b first takes item b (no atomic);
@@ -185,6 +201,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks,
       atomicAdd(&gb->gen, 1u);
     } else {
       unsigned long long t0 = globaltimer_ns();
+      unsigned int nap = 32;
       while (ld_acquire_u32(&gb->gen) == my_gen) {
         if (ld_volatile_i32(&gb->abort)) { ok = 0; break; }
         if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
@@ -193,7 +210,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks,
           ok = 0;
           break;
         }
-        __nanosleep(40);
+        __nanosleep(nap);
+        if (nap < 128) nap <<= 1;
       }
     }
     __threadfence();

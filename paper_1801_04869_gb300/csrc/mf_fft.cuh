@@ -3,10 +3,10 @@
 // every row, column and z pass.
 //
 // A CTA of NT threads transforms `nlines` lines of length L (a power of two, 2..4096) that
-// sit back to back in shared memory (element e at position sp(e)), nlines * L <= BATCH.  Stages alternate between two
-// shared buffers (each thread keeps one butterfly in registers).  Twiddles come from a global table
-// tw[m] = exp(-2 pi i m / L) (read-only, cached); the inverse uses their conjugates and is
-// unnormalised.
+// sit back to back in shared memory (element e at position sp(e)), nlines * L <= BATCH.
+// Stages alternate between two shared buffers (each thread keeps one butterfly in registers).
+// Twiddles come from a read-only global table in stage order (mf_tables.h), so the lanes of a
+// warp read consecutive entries; the inverse uses their conjugates and is unnormalised.
 #pragma once
 #include "mf_common.cuh"
 
@@ -90,7 +90,8 @@ __device__ __forceinline__ void dft(C2<T>* v) {
 // one Stockham stage of radix R from `in` to `out`; p = 2^lgp = product of the radices
 // already applied.  Butterfly b of line `line` reads in[i + j L/R] (j < R), multiplies by
 // w^(j k) with k = i mod p and w = exp(DIR 2 pi i / (p R)), and writes its length-R DFT to
-// out[(i - k) R + k + j p].
+// out[(i - k) R + k + j p].  `tw` is the stage's block of the stage-ordered table: entry
+// (j - 1) p + k holds w^(j k) for the forward direction.
 template <typename T, int R, int LGR, int DIR>
 __device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, int lgp, int nlines,
                                           const C2<T>* __restrict__ tw) {
@@ -106,11 +107,10 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, 
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = in[sp(src + (j << lgq))];
     if (lgp > 0) {
-      // w^(j k) = tw[j k L / (p R)] (conjugated for DIR > 0)
-      const int step = k << (lgL - lgp - LGR);
+      // w^(j k) from the stage's block of the stage-ordered table (conjugated for DIR > 0)
 #pragma unroll
       for (int j = 1; j < R; ++j) {
-        C2<T> w = tw[j * step];
+        C2<T> w = ldg_c2(tw + (((j - 1) << lgp) + k));
         if (DIR > 0) w.y = -w.y;
         v[j] = cmul(v[j], w);
       }
@@ -131,22 +131,23 @@ __device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines
                                          const C2<T>* __restrict__ tw) {
   int lgp = 0;
   int rem = lgL;
+  int off = 0;                       // block of the current stage in the stage-ordered table
   C2<T>* in = a;
   C2<T>* out = b;
   while (rem > 0) {
     if (sizeof(T) == 4 && rem >= 4 && rem != 5) {
       // single precision: radix 16 (three shared-memory passes for 2048 points)
-      fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw);
-      lgp += 4; rem -= 4;
+      fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      off += 15 << lgp; lgp += 4; rem -= 4;
     } else if (rem >= 3) {
-      fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw);
-      lgp += 3; rem -= 3;
+      fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      off += 7 << lgp; lgp += 3; rem -= 3;
     } else if (rem == 2) {
-      fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw);
-      lgp += 2; rem -= 2;
+      fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      off += 3 << lgp; lgp += 2; rem -= 2;
     } else {
-      fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw);
-      lgp += 1; rem -= 1;
+      fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      off += 1 << lgp; lgp += 1; rem -= 1;
     }
     C2<T>* t = in; in = out; out = t;
   }
@@ -199,10 +200,9 @@ __device__ __forceinline__ void fft_stage_io(int lgL, int lgp, int nlines, const
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = ld(line, i + (j << lgq));
     if (lgp > 0) {
-      const int step = k << (lgL - lgp - LGR);
 #pragma unroll
       for (int j = 1; j < R; ++j) {
-        C2<T> w = tw[j * step];
+        C2<T> w = ldg_c2(tw + (((j - 1) << lgp) + k));
         if (DIR > 0) w.y = -w.y;
         v[j] = cmul(v[j], w);
       }
@@ -243,9 +243,10 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in, C2<T>* out, int lgL,
       const int base = ((f * nl + l) << lgL) + i;
 #pragma unroll
       for (int j = 0; j < R; ++j) x[f][j] = in[sp(base + (j << lgq))];
-      // twiddles of the last forward stage: p = q, k = i, w^(j i) with w = exp(-2 pi i / L)
+      // twiddles of the last forward stage (p = q, k = i), from its block of the table
 #pragma unroll
-      for (int j = 1; j < R; ++j) x[f][j] = cmul(x[f][j], tw[j * i]);
+      for (int j = 1; j < R; ++j)
+        x[f][j] = cmul(x[f][j], ldg_c2(tw + (((j - 1) << lgq) + i)));
       dft<T, R, -1>(x[f]);
     }
     C2<T> y[NFO][R];
@@ -280,49 +281,63 @@ __device__ __forceinline__ void fft_middle_any(int lgr, const C2<T>* in, C2<T>* 
   else fft_middle<T, 2, 1, NFI, NFO>(in, out, lgL, nl, tw, mul);
 }
 
-// Round trip F^-1[M F(.)] of NFI -> NFO fields on nl line groups, global in and out:
-// gsrc(f, l) / gdst(g, l) give the first element of field f / g of group l (contiguous lines).
-// Needs a plan of at least two stages.
-template <typename T, int NFI, int NFO, class Src, class Dst, class Mul>
+// Round trip F^-1[M F(.)] of NFI -> NFO fields on nl line groups:
+// gsrc(f, l) / gdst(g, l) give the first element of field f / g of group l (contiguous lines,
+// global or shared memory); after_first() runs (in every thread) once the first stage has
+// consumed the source.  Needs a plan of at least two stages.
+template <typename T, int NFI, int NFO, class Src, class Dst, class Mul, class AfterFirst>
 __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T>* __restrict__ tw,
-                               Src gsrc, Dst gdst, Mul mul) {
+                               Src gsrc, Dst gdst, Mul mul, AfterFirst after_first) {
   const FftPlan P = fft_plan<T>(lgL);
-  const int L = 1 << lgL;
+  // block offsets in table A (plan order) and table B (reversed plan, right after A)
+  int offA[8], offB[8];
+  int lenA = 0;
+  {
+    int lgp = 0;
+    for (int s = 0; s < P.m; ++s) { offA[s] = lenA; lenA += ((1 << P.lgr[s]) - 1) << lgp; lgp += P.lgr[s]; }
+    int lenB = lenA, lgq = 0;
+    for (int s = 0; s < P.m; ++s) {
+      const int l = P.lgr[P.m - 1 - s];
+      offB[s] = lenB; lenB += ((1 << l) - 1) << lgq; lgq += l;
+    }
+  }
   int lgp = 0;
-  // forward stage 0: global -> sa
-  fft_stage_io_any<T, -1>(P.lgr[0], lgL, 0, NFI * nl, tw,
+  // forward stage 0: source -> sa
+  fft_stage_io_any<T, -1>(P.lgr[0], lgL, 0, NFI * nl, tw + offA[0],
       [&](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
       [&](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
+  after_first();                     // the source of the first stage is no longer needed
   lgp += P.lgr[0];
   C2<T>* cur = sa;
   C2<T>* oth = sb;
   for (int s = 1; s < P.m - 1; ++s) {
     const int lgr = P.lgr[s];
-    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
-    else if (lgr == 3) fft_stage<T, 8, 3, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
-    else if (lgr == 2) fft_stage<T, 4, 2, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
-    else fft_stage<T, 2, 1, -1>(cur, oth, lgL, lgp, NFI * nl, tw);
+    const C2<T>* t = tw + offA[s];
+    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, -1>(cur, oth, lgL, lgp, NFI * nl, t);
+    else if (lgr == 3) fft_stage<T, 8, 3, -1>(cur, oth, lgL, lgp, NFI * nl, t);
+    else if (lgr == 2) fft_stage<T, 4, 2, -1>(cur, oth, lgL, lgp, NFI * nl, t);
+    else fft_stage<T, 2, 1, -1>(cur, oth, lgL, lgp, NFI * nl, t);
     lgp += lgr;
-    C2<T>* t = cur; cur = oth; oth = t;
+    C2<T>* tt = cur; cur = oth; oth = tt;
   }
-  // forward last stage + multiplier + inverse first stage
-  fft_middle_any<T, NFI, NFO>(P.lgr[P.m - 1], cur, oth, lgL, nl, tw, mul);
-  { C2<T>* t = cur; cur = oth; oth = t; }
+  // forward last stage + multiplier + inverse first stage (p = 1: no twiddles)
+  fft_middle_any<T, NFI, NFO>(P.lgr[P.m - 1], cur, oth, lgL, nl, tw + offA[P.m - 1], mul);
+  { C2<T>* tt = cur; cur = oth; oth = tt; }
   int lgpi = P.lgr[P.m - 1];
   for (int s = P.m - 2; s >= 1; --s) {
     const int lgr = P.lgr[s];
-    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
-    else if (lgr == 3) fft_stage<T, 8, 3, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
-    else if (lgr == 2) fft_stage<T, 4, 2, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
-    else fft_stage<T, 2, 1, +1>(cur, oth, lgL, lgpi, NFO * nl, tw);
+    const C2<T>* t = tw + offB[P.m - 1 - s];
+    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
+    else if (lgr == 3) fft_stage<T, 8, 3, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
+    else if (lgr == 2) fft_stage<T, 4, 2, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
+    else fft_stage<T, 2, 1, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
     lgpi += lgr;
-    C2<T>* t = cur; cur = oth; oth = t;
+    C2<T>* tt = cur; cur = oth; oth = tt;
   }
-  // inverse last stage: shared -> global
-  fft_stage_io_any<T, +1>(P.lgr[0], lgL, lgpi, NFO * nl, tw,
+  // inverse last stage: shared -> destination
+  fft_stage_io_any<T, +1>(P.lgr[0], lgL, lgpi, NFO * nl, tw + offB[P.m - 1],
       [&](int line, int pos) { return cur[sp((line << lgL) + pos)]; },
       [&](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
-  (void)L;
 }
 
 }  // namespace mf

@@ -53,8 +53,8 @@ struct Film {
     Sa = (C2<T>*)d.Sa; Sb = (C2<T>*)d.Sb;
     hd = (T*)d.hd; u = (T*)d.u; q1 = (const T*)d.q1; q2 = (const T*)d.q2;
     mask = d.mask; jcmap = (const T*)d.jcmap;
-    twx = sm + 2 * BATCH_PAD;                   // twiddle tables copied to shared memory
-    twy = twx + nx;
+    twx = (const C2<T>*)d.tw_x;                 // stage-ordered twiddle tables (read-only)
+    twy = (const C2<T>*)d.tw_y;
     ktab = (const T*)d.ktab;
     gtab = (const T*)d.gtab;
     rb1 = d.rows_per_item;
@@ -67,7 +67,7 @@ struct Film {
 
   // ---- y pass: forward, multiplier, inverse on nl consecutive x-wavenumber lines ----
   // shared line f * nl + l holds field f of line kx0 + l
-  __device__ void col_item(int kx0, int nl, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
+  __device__ __noinline__ void col_item(int kx0, int nl, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
     if (fft_plan<T>(lgy).m >= 2) {
       // fused round trip: global -> first stage, multiplier between the forward last and the
       // inverse first stage, last stage -> global
@@ -88,7 +88,7 @@ struct Film {
               T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
               y[0] = cmul_si(cscale(x[0], kxo * G * s), 1);
               y[1] = cmul_si(cscale(x[0], kyo * G * s), 1);
-            });
+            }, [] {});
       } else if (op == OP_CURLNEG) {
         fft_round_trip<T, 2, 1>(sm, sm2, lgy, nl, twy, src, dst,
             [&](int l, int ky, const C2<T>* x, C2<T>* y) {
@@ -96,7 +96,7 @@ struct Film {
               // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
               const C2<T> c = {kyo * x[0].x - kxo * x[1].x, kyo * x[0].y - kxo * x[1].y};
               y[0] = cmul_si(cscale(c, G * s), 1);
-            });
+            }, [] {});
       } else {
         fft_round_trip<T, 1, 1>(sm, sm2, lgy, nl, twy, src, dst,
             [&](int l, int ky, const C2<T>* x, C2<T>* y) {
@@ -108,7 +108,7 @@ struct Film {
               else if (op == OP_KH) m = kabs * (T)0.5;
               else m = (T)1;
               y[0] = cscale(x[0], m * s);
-            });
+            }, [] {});
       }
       return;
     }
@@ -178,7 +178,7 @@ struct Film {
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
   // epi(row, x, in[], out[]) is called for every cell of the item.
   template <int NIN, int NOUT, class Epi>
-  __device__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi) {
+  __device__ __noinline__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi) {
     const int npair = rb / 2;
     C2<T>* X = sm;
     const int lgpair = __ffs(npair) - 1;
@@ -564,9 +564,6 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
     sh.A_prev = st->A_prev;
   }
   __syncthreads();
-  table_to_smem<T>(sm + 2 * BATCH_PAD, (const C2<T>*)d.tw_x, d.nx);
-  table_to_smem<T>(sm + 2 * BATCH_PAD + d.nx, (const C2<T>*)d.tw_y, d.ny);
-  __syncthreads();
   Film<T> F(d, sm, sh);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int status = ST_OK;
@@ -618,9 +615,9 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
 }
 
 size_t kernel_smem_bytes(const Desc& d) {
-  // two FFT buffers, then the twiddle tables of the three axes
+  // the two FFT buffers (twiddles stay in global memory, read through L1)
   const size_t c = d.precision ? sizeof(C2<float>) : sizeof(C2<double>);
-  return (2 * (size_t)BATCH_PAD + d.nx + d.ny + d.nz) * c;
+  return 2 * (size_t)BATCH_PAD * c;
 }
 
 int film_max_blocks(int precision, size_t smem) {

@@ -23,6 +23,7 @@
 
 #include "../../include/mf.h"
 #include "mf_common.cuh"
+#include "mf_tables.h"
 
 using namespace mf;
 
@@ -92,7 +93,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   const size_t oSa = take(2 * nspec * 2 * ts), oSb = take(2 * nspec * 2 * ts);
   const size_t ohd = take(ncell * ts), ou = take(ncell * ts), oq1 = take(ncell * ts), oq2 = take(ncell * ts);
   const size_t ojc = take(p->jc_map ? ncell * ts : 0), omask = take(ncell);
-  const size_t otwx = take(nx * 2 * ts), otwy = take(ny * 2 * ts), otwz = take(2 * ts);
+  const size_t otwx = take(2 * nx * 2 * ts), otwy = take(2 * ny * 2 * ts), otwz = take(2 * ts);
   const size_t okt = take(nk * ts), ogt = take(nk * ts);
   const size_t opart = take((size_t)8 * ny * 8), ost = take(sizeof(SolverState)), ogb = take(sizeof(GridBarrier));
   const size_t oknots = take(2 * (size_t)(p->he_knots > 0 ? p->he_knots : 1) * 8);
@@ -157,20 +158,21 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   };
   copy_sync(w + omask, p->mask, (size_t)ncell);
   {
-    double tw[2 * NOALLOC_MAX_N], kt[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1],
+    double tw[4 * NOALLOC_MAX_N], kt[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1],
         gt[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1];
-    float twf[2 * NOALLOC_MAX_N], ktf[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1],
+    float twf[4 * NOALLOC_MAX_N], ktf[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1],
         gtf[NOALLOC_MAX_N / 2 + 1 + NOALLOC_MAX_N + 1];
     const int ns[2] = {nx, ny};
     const size_t to[2] = {otwx, otwy};
     for (int a = 0; a < 2; ++a) {
-      for (int j = 0; j < ns[a]; ++j) {
-        const double ang = -2.0 * M_PI * (double)j / (double)ns[a];
-        tw[2 * j] = std::cos(ang); tw[2 * j + 1] = std::sin(ang);
-        twf[2 * j] = (float)tw[2 * j]; twf[2 * j + 1] = (float)tw[2 * j + 1];
+      // stage-ordered twiddle tables (A then B), as mf_create writes them
+      if (precision) {
+        const int n = stage_twiddles<float>(ns[a], twf);
+        copy_sync(w + to[a], twf, (size_t)n * 2 * 4);
+      } else {
+        const int n = stage_twiddles<double>(ns[a], tw);
+        copy_sync(w + to[a], tw, (size_t)n * 2 * 8);
       }
-      if (precision) copy_sync(w + to[a], twf, (size_t)ns[a] * 2 * 4);
-      else copy_sync(w + to[a], tw, (size_t)ns[a] * 2 * 8);
     }
     int c = 0;
     const double Ls[2] = {p->Lx, p->Ly};

@@ -141,11 +141,6 @@ __device__ __forceinline__ void gather_batched(C2<T>* sm, const C2<T>* src, int 
   __syncthreads();
 }
 
-// Copy `n` complex values of a global table into shared memory (start of a launch).
-template <typename T>
-__device__ __forceinline__ void table_to_smem(C2<T>* dst, const C2<T>* __restrict__ src, int n) {
-  for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
-}
 
 // ------------------------------------------------------------------------------------------
 // four consecutive cells: vector loads and stores (index a multiple of 4, 16-byte aligned)
