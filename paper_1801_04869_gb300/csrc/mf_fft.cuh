@@ -304,8 +304,8 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
   int lgp = 0;
   // forward stage 0: source -> sa
   fft_stage_io_any<T, -1>(P.lgr[0], lgL, 0, NFI * nl, tw + offA[0],
-      [&](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
-      [&](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
+      [=](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
+      [=](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
   after_first();                     // the source of the first stage is no longer needed
   lgp += P.lgr[0];
   C2<T>* cur = sa;
@@ -335,9 +335,10 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // inverse last stage: shared -> destination
+  const C2<T>* const last = cur;
   fft_stage_io_any<T, +1>(P.lgr[0], lgL, lgpi, NFO * nl, tw + offB[P.m - 1],
-      [&](int line, int pos) { return cur[sp((line << lgL) + pos)]; },
-      [&](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
+      [=](int line, int pos) { return last[sp((line << lgL) + pos)]; },
+      [=](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
 }
 
 }  // namespace mf

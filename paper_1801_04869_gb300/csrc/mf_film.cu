@@ -22,6 +22,18 @@ namespace mf {
 
 enum Op2 { OP_GRAD = 0, OP_CURLNEG = 1, OP_K1 = 2, OP_K2 = 3, OP_KH = 4, OP_ID = 5 };
 
+// raw pointers and sizes the x-pass epilogues need, held by value (registers)
+template <typename T>
+struct FilmPtrs {
+  const uint8_t* mask;
+  const T* jcmap;
+  T* hd;
+  T* u;
+  const T* q1;
+  const T* q2;
+  int nx;
+};
+
 template <typename T>
 struct Film {
   const Desc& d;
@@ -65,16 +77,24 @@ struct Film {
 
   __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
 
+  __device__ FilmPtrs<T> ptrs() const { return FilmPtrs<T>{mask, jcmap, hd, u, q1, q2, nx}; }
+
   // ---- y pass: forward, multiplier, inverse on nl consecutive x-wavenumber lines ----
   // shared line f * nl + l holds field f of line kx0 + l
   __device__ __noinline__ void col_item(int kx0, int nl, const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
     if (fft_plan<T>(lgy).m >= 2) {
       // fused round trip: global -> first stage, multiplier between the forward last and the
-      // inverse first stage, last stage -> global
-      auto src = [&](int f, int l) { return Sin + f * nspec + (long long)(kx0 + l) * ny; };
-      auto dst = [&](int g, int l) { return Sout + g * nspec + (long long)(kx0 + l) * ny; };
+      // inverse first stage, last stage -> global.  Everything the lambdas use is a copy held
+      // in registers.
+      const long long nspec = this->nspec;
+      const int ny = this->ny, nkx = this->nkx, half = this->half;
+      const T* const ktab = this->ktab;
+      const T* const gtab = this->gtab;
+      const T lam = (T)d.lam;
+      auto src = [=](int f, int l) { return Sin + f * nspec + (long long)(kx0 + l) * ny; };
+      auto dst = [=](int g, int l) { return Sout + g * nspec + (long long)(kx0 + l) * ny; };
       const T s = (T)1 / (T)ncell;
-      auto coef = [&](int l, int ky, T& kxo, T& kyo, T& k2, T& G) {
+      auto coef = [=](int l, int ky, T& kxo, T& kyo, T& k2, T& G) {
         const int kx = kx0 + l;
         const T kxv = __ldg(&ktab[kx]), kyv = __ldg(&ktab[nkx + ky]);
         kxo = (kx == half) ? (T)0 : kxv;
@@ -84,14 +104,14 @@ struct Film {
       };
       if (op == OP_GRAD) {
         fft_round_trip<T, 1, 2>(sm, sm2, lgy, nl, twy, src, dst,
-            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+            [=](int l, int ky, const C2<T>* x, C2<T>* y) {
               T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
               y[0] = cmul_si(cscale(x[0], kxo * G * s), 1);
               y[1] = cmul_si(cscale(x[0], kyo * G * s), 1);
             }, [] {});
       } else if (op == OP_CURLNEG) {
         fft_round_trip<T, 2, 1>(sm, sm2, lgy, nl, twy, src, dst,
-            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+            [=](int l, int ky, const C2<T>* x, C2<T>* y) {
               T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
               // -(i kx G e_y - i ky G e_x) = i G (ky e_x - kx e_y)
               const C2<T> c = {kyo * x[0].x - kxo * x[1].x, kyo * x[0].y - kxo * x[1].y};
@@ -99,12 +119,12 @@ struct Film {
             }, [] {});
       } else {
         fft_round_trip<T, 1, 1>(sm, sm2, lgy, nl, twy, src, dst,
-            [&](int l, int ky, const C2<T>* x, C2<T>* y) {
+            [=](int l, int ky, const C2<T>* x, C2<T>* y) {
               T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
               const T kabs = sqrt(k2);
               T m;
               if (op == OP_K1) m = (k2 > (T)0) ? (T)2 / kabs : (T)0;
-              else if (op == OP_K2) m = (T)d.lam * kabs * (T)0.5 * G;
+              else if (op == OP_K2) m = lam * kabs * (T)0.5 * G;
               else if (op == OP_KH) m = kabs * (T)0.5;
               else m = (T)1;
               y[0] = cscale(x[0], m * s);
@@ -178,12 +198,19 @@ struct Film {
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
   // epi(row, x, in[], out[]) is called for every cell of the item.
   template <int NIN, int NOUT, class Epi>
-  __device__ __noinline__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi) {
+  __device__ __noinline__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi_io) {
+    // work on register copies: the epilogue and the members used in the loops
+    Epi epi = epi_io;
+    C2<T>* const smA = sm;
+    C2<T>* const smB = sm2;
+    const int nx = this->nx, lgx = this->lgx, ny = this->ny;
+    const long long nspec = this->nspec;
+    const C2<T>* const twx = this->twx;
     const int npair = rb / 2;
-    C2<T>* X = sm;
+    C2<T>* X = smA;
     const int lgpair = __ffs(npair) - 1;
-    if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(sm, sm2, Sin + y0, nspec, ny, npair, lgpair, lgx, twx);
-    C2<T>* Y = X == sm ? sm2 : sm;
+    if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(smA, smB, Sin + y0, nspec, ny, npair, lgpair, lgx, twx);
+    C2<T>* Y = X == smA ? smB : smA;
     // four consecutive cells of both rows of a pair per step; the epilogue issues its global
     // loads for the four cells together
     const int lgq = lgx - 2;
@@ -210,6 +237,8 @@ struct Film {
     }
     __syncthreads();
     if constexpr (NOUT > 0) rows_forward_scatter<T, NOUT>(X, Y, Sout + y0, nspec, ny, npair, lgpair, lgx, twx);
+    epi_io.acc = epi.acc;
+    epi_io.accmax = epi.accmax;
   }
 
   // rows pass with an optional per-item reduction into partials slot `slot`
@@ -241,7 +270,7 @@ struct Film {
 // P1 / readouts: field from the FP64 stage input
 template <typename T>
 struct EpiStage : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   StageIn in;
   __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
     V4<double> v = ld4(in.y + i);
@@ -259,9 +288,9 @@ struct EpiStage : EpiBase<T> {
 // mask indicator of free space (set-up of q1, q2)
 template <typename T>
 struct EpiOut : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
-    const uchar4 m = ldmask4(F->mask + i);
+    const uchar4 m = ldmask4(P.mask + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q) out[0].v[q] = mask_at(m, q) == 0 ? (T)1 : (T)0;
   }
@@ -270,14 +299,14 @@ struct EpiOut : EpiBase<T> {
 // store a real field (set-up)
 template <typename T>
 struct EpiStoreT : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   T* dst;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>*) { st4(dst + i, in[0]); }
 };
 // h_z readout (FP64)
 template <typename T>
 struct EpiStoreHz : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   double* dst;
   double he;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
@@ -291,12 +320,12 @@ struct EpiStoreHz : EpiBase<T> {
 // P3: power law
 template <typename T>
 struct EpiPower : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   T n, e0, jc, rho_out;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(F->mask + i);
+    const uchar4 m = ldmask4(P.mask + i);
     V4<T> jcl;
-    if (F->jcmap) jcl = ldg4(F->jcmap + i);
+    if (P.jcmap) jcl = ldg4(P.jcmap + i);
     else jcl = V4<T>{{jc, jc, jc, jc}};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -312,13 +341,13 @@ struct EpiPower : EpiBase<T> {
 // P5: initial h_dot (warm start), sum over D
 template <typename T>
 struct EpiInit : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   bool warm;
   T A_prev, hed;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(F->mask + i);
+    const uchar4 m = ldmask4(P.mask + i);
     V4<T> w;
-    if (warm) w = ld4(F->hd + i);
+    if (warm) w = ld4(P.hd + i);
     V4<T> h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -326,7 +355,7 @@ struct EpiInit : EpiBase<T> {
       else h.v[q] = warm ? w.v[q] - A_prev : hed;             // warm start (Section 2.2)
       this->acc += (double)h.v[q];
     }
-    st4(F->hd + i, h);
+    st4(P.hd + i, h);
     out[0] = h;
   }
 };
@@ -334,11 +363,11 @@ struct EpiInit : EpiBase<T> {
 // P7: u = raw - A q1; sum over free space; forward of mask_out u
 template <typename T>
 struct EpiU : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   T A;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(F->mask + i);
-    const V4<T> q1 = ldg4(F->q1 + i);
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> q1 = ldg4(P.q1 + i);
     V4<T> v;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -347,18 +376,18 @@ struct EpiU : EpiBase<T> {
       if (o) this->acc += (double)v.v[q];
       out[0].v[q] = o ? v.v[q] : (T)0;
     }
-    st4(F->u + i, v);
+    st4(P.u + i, v);
   }
 };
 
 // P8: residual sum over free space of |u - C|
 template <typename T>
 struct EpiResid : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   double C;
   __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
-    const uchar4 m = ldmask4(F->mask + i);
-    const V4<T> u = ld4(F->u + i);
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> u = ld4(P.u + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (mask_at(m, q) == 0) this->acc += fabs((double)u.v[q] - C);
@@ -368,12 +397,12 @@ struct EpiResid : EpiBase<T> {
 // P10: h_dot update on free space (Eq. 12), sum over D, forward
 template <typename T>
 struct EpiUpdate : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   T A, C;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(F->mask + i);
-    V4<T> h = ld4(F->hd + i);
-    const V4<T> q2 = ldg4(F->q2 + i);
+    const uchar4 m = ldmask4(P.mask + i);
+    V4<T> h = ld4(P.hd + i);
+    const V4<T> q2 = ldg4(P.q2 + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (mask_at(m, q) == 0) {
@@ -382,7 +411,7 @@ struct EpiUpdate : EpiBase<T> {
       }
       this->acc += (double)h.v[q];
     }
-    st4(F->hd + i, h);
+    st4(P.hd + i, h);
     out[0] = h;
   }
 };
@@ -390,7 +419,7 @@ struct EpiUpdate : EpiBase<T> {
 // finalize: g_dot = (u - C) on the conductor; optional BS23 error contribution
 template <typename T>
 struct EpiFinal : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   double C;
   double* kout;
   // error estimate (stage 4 of a step): E = h (e1 k1 + e2 k2 + e3 k3 + e4 k4)
@@ -398,8 +427,8 @@ struct EpiFinal : EpiBase<T> {
   double h, rtol, atol;
   const double* k1; const double* k2; const double* k3; const double* y; const double* ynew;
   __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
-    const uchar4 m = ldmask4(F->mask + i);
-    const V4<T> u = ld4(F->u + i);
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> u = ld4(P.u + i);
     V4<double> g;
 #pragma unroll
     for (int q = 0; q < 4; ++q) g.v[q] = mask_at(m, q) != 0 ? (double)u.v[q] - C : 0.0;
@@ -425,7 +454,7 @@ struct EpiFinal : EpiBase<T> {
 // magnetization: sum over D of g (times dx dy on the host side)
 template <typename T>
 struct EpiMoment : EpiBase<T> {
-  const Film<T>* F;
+  FilmPtrs<T> P;
   const double* g;
   __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
     const V4<double> v = ld4(g + i);
@@ -449,14 +478,14 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   // P1
   {
-    EpiStage<T> e; e.F = &F; e.in = sin;
+    EpiStage<T> e; e.P = F.ptrs(); e.in = sin;
     F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, -1);
   }
   if (!F.sync(1)) { res.status = ST_BARRIER; return res; }
   F.cols(F.Sa, 1, F.Sa, 2, OP_GRAD);                                    // P2
   if (!F.sync(2)) { res.status = ST_BARRIER; return res; }
   {
-    EpiPower<T> e; e.F = &F;
+    EpiPower<T> e; e.P = F.ptrs();
     e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
     F.rows<2, 2>(F.rb2, F.Sa, F.Sb, e, -1);                             // P3
   }
@@ -466,7 +495,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   const bool have_out = d.nout > 0;
   {
-    EpiInit<T> e; e.F = &F;
+    EpiInit<T> e; e.P = F.ptrs();
     e.warm = F.sh.warm_valid != 0; e.A_prev = (T)F.sh.A_prev; e.hed = (T)hed;
     F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                              // P5
   }
@@ -482,7 +511,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                    // P6
     if (!F.sync(6)) { res.status = ST_BARRIER; return res; }
     {
-      EpiU<T> e; e.F = &F; e.A = (T)A;
+      EpiU<T> e; e.P = F.ptrs(); e.A = (T)A;
       F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 1);                            // P7
     }
     if (!F.sync(7)) { res.status = ST_BARRIER; return res; }
@@ -490,7 +519,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     C = F.total(1, F.rb1) / nout;                                       // Eq. 11
     {
       // P8 (residual, row items) and P9 (K2 column items) share one phase and one item space
-      EpiResid<T> e; e.F = &F; e.C = C;
+      EpiResid<T> e; e.P = F.ptrs(); e.C = C;
       const int nl9 = F.col_lines(1);
       const int n8 = F.ny / F.rb1, n9 = (F.nkx + nl9 - 1) / nl9;
       for (int it = F.wq.begin(n8 + n9); it < n8 + n9; it = F.wq.next(d.gb, &F.sh.item)) {
@@ -512,7 +541,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     const bool stop = (forced || fixed) ? last : (r < d.iter_tol || last);
     if (stop) break;
     {
-      EpiUpdate<T> e; e.F = &F; e.A = (T)A; e.C = (T)C;
+      EpiUpdate<T> e; e.P = F.ptrs(); e.A = (T)A; e.C = (T)C;
       F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                            // P10
     }
     if (!F.sync(10)) { res.status = ST_BARRIER; return res; }
@@ -527,7 +556,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   // finalize
   {
-    EpiFinal<T> e; e.F = &F; e.C = C; e.kout = kout; e.is_max = true;
+    EpiFinal<T> e; e.P = F.ptrs(); e.C = C; e.kout = kout; e.is_max = true;
     e.err = want_err; e.h = h_err; e.rtol = d.rtol; e.atol = d.atol;
     e.k1 = e_k1; e.k2 = e_k2; e.k3 = e_k3; e.y = e_y; e.ynew = e_ynew;
     F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 3);
@@ -571,27 +600,27 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
   if (a.mode == MODE_SETUP) {
     // q1 = F^-1[K1 F(out)], q2 = F^-1[K2 F(out)]
     for (int pass = 0; pass < 2; ++pass) {
-      EpiOut<T> eo; eo.F = &F;
+      EpiOut<T> eo; eo.P = F.ptrs();
       F.rows<0, 1>(F.rb1, nullptr, F.Sa, eo, -1);
       if (!F.sync(20)) { status = ST_BARRIER; break; }
       F.cols(F.Sa, 1, F.Sa, 1, pass == 0 ? OP_K1 : OP_K2);
       if (!F.sync(21)) { status = ST_BARRIER; break; }
-      EpiStoreT<T> es; es.F = &F; es.dst = (T*)(pass == 0 ? d.q1 : d.q2);
+      EpiStoreT<T> es; es.P = F.ptrs(); es.dst = (T*)(pass == 0 ? d.q1 : d.q2);
       F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
       if (!F.sync(22)) { status = ST_BARRIER; break; }
     }
   } else if (a.mode == MODE_HZ) {
-    EpiStage<T> e; e.F = &F; e.in = StageIn{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    EpiStage<T> e; e.P = F.ptrs(); e.in = StageIn{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
     F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, -1);
     if (F.sync(30)) {
       F.cols(F.Sa, 1, F.Sa, 1, OP_KH);
       if (F.sync(31)) {
-        EpiStoreHz<T> es; es.F = &F; es.dst = a.out; es.he = he_value(d, a.t);
+        EpiStoreHz<T> es; es.P = F.ptrs(); es.dst = a.out; es.he = he_value(d, a.t);
         F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
       } else status = ST_BARRIER;
     } else status = ST_BARRIER;
   } else if (a.mode == MODE_MOMENT) {
-    EpiMoment<T> e; e.F = &F; e.g = a.y_in;
+    EpiMoment<T> e; e.P = F.ptrs(); e.g = a.y_in;
     F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 4);
     if (F.sync(40)) {
       const double s = F.total(4, F.rb1);
