@@ -14,7 +14,8 @@ and handles a failed outside iteration by letting the step control shrink the st
 
 Step control (a standard choice; the paper states none):
   accept: h <- h min(5, max(0.2, 0.9 err^(-1/3))), capped at 1x right after a rejection
-  reject: h <- h max(0.2, 0.9 err^(-1/3));  non-converged stage: h <- h/2
+  reject: h <- h max(0.2, 0.9 err^(-1/3));  non-converged stage (k1 included): h <- h/2, and
+  a non-converged k1 is evaluated again on the next attempt (its warm start has advanced)
   h < h_min stops with STEP_UNDERFLOW.
 Steps are clipped so that they end exactly on the next output time or h_e knot (a step within
 10% of reaching it is stretched to it).  A step that ends on a knot discards k4 as the next k1,
@@ -89,13 +90,16 @@ class BS23:
         it = [-1, -1, -1, -1]
         fi = (lambda s: None) if forced is None else (lambda s: forced.iters[s])
 
+        st = OK
         if self.k1 is None or (forced is not None and forced.iters[0] >= 0):
-            self.k1, it[0], st = self._f(t, y, seg, fi(0))
-            if st != OK:
-                raise RuntimeError("outside iteration failed at the start of a step")
+            # a non-converged k1 rejects the attempt like any stage (Section 2.2: the step
+            # control reacts, and the warm-started iteration continues on the next attempt)
+            k1v, it[0], st = self._f(t, y, seg, fi(0))
+            self.k1 = k1v if st == OK else None
         k1 = self.k1
         outcome = ACCEPT
-        k2, it[1], st = self._f(t + 0.5 * h, y + 0.5 * h * k1, seg, fi(1))
+        if st == OK:
+            k2, it[1], st = self._f(t + 0.5 * h, y + 0.5 * h * k1, seg, fi(1))
         if st == OK:
             k3, it[2], st = self._f(t + 0.75 * h, y + 0.75 * h * k2, seg, fi(2))
         if st == OK:

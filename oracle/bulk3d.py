@@ -16,7 +16,8 @@ Readings where the paper is silent (also in the design doc):
     Phi carries no Gaussian;
   * the conductor (mask 1 superconductor, mask 2 normal cutting layer) keeps h_dot_in and
     contributes to j_dot_in; the iteration updates free space (mask 0) only;
-  * warm start from the most recent call (first call: h_e_dot); h_dot after the last update is
+  * warm start from the most recent call (first call: h_e_dot), dropped after a call that fails
+    with a residual above 1e3 times the threshold (or not finite); h_dot after the last update is
     returned on all of D;
   * iter_tol <= 0 runs exactly iter_max iterations and reports OK;
   * magnetization m = 1/2 sum dV r x j over the conductor.
@@ -137,6 +138,8 @@ class BulkProblem:
             if r < thresh:
                 break
         status = OK if (fixed or self.iter_tol <= 0.0 or r < thresh) else NOCONV
+        if status == NOCONV and not (r < 1e3 * thresh):
+            self.warm = None       # a diverged iterate is no warm start; the next call starts cold
         self.last = dict(r=r, thresh=thresh)
         return hd, i + 1, status
 

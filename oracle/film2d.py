@@ -21,6 +21,7 @@ Readings where the paper is silent (each also listed in the design doc):
   * 2/|k| and the A, C constants are zero/absent at k = 0;
   * the returned g_dot is zeroed on free space (g stays exactly 0 there);
   * the warm start is the converged free-space h_dot of the most recent call (first call: h_e_dot);
+    a call that fails with a residual above 1e3 tol (or not finite) leaves no warm start;
   * the iteration stops without an update when it converges or reaches iter_max (then NOCONV);
   * iter_tol <= 0 runs exactly iter_max iterations and reports OK;
   * no free-space cells: a single pass with C = A = 0.
@@ -154,6 +155,8 @@ class FilmProblem:
             hd = np.where(self.out, hd - A, hd)
             self.warm = hd.copy()
         status = OK if (fixed or self.iter_tol <= 0.0 or r < self.iter_tol) else NOCONV
+        if status == NOCONV and not (r < 1e3 * self.iter_tol):
+            self.warm = None       # a diverged iterate is no warm start; the next call starts cold
         self.last = dict(C=C, A=A, r=r, hdot=hd)
         return np.where(self.conductor, gd, 0.0), i + 1, status
 

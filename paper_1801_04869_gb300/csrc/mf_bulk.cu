@@ -22,6 +22,17 @@ namespace mf {
 
 enum Op3 { OP3_CURL = 0, OP3_CURLNEG = 1, OP3_PHI = 2 };
 
+// raw pointers and sizes the x-pass epilogues need, held by value (registers)
+template <typename T>
+struct BulkPtrs {
+  const uint8_t* mask;
+  const T* jcmap;
+  T* hd;
+  long long ncell;
+  int nx, ny;
+  double Lx, Ly, Lz, dx, dy, dz;
+};
+
 template <typename T>
 struct Bulk {
   const Desc& d;
@@ -67,9 +78,20 @@ struct Bulk {
 
   __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
 
+  __device__ BulkPtrs<T> ptrs() const {
+    return BulkPtrs<T>{mask, jcmap, hd, ncell, nx, ny, d.Lx, d.Ly, d.Lz, d.dx, d.dy, d.dz};
+  }
+
   // ---- x pass over rows (z, y0 .. y0 + rb): inverse of NIN = 0|3 fields, epilogue, forward ----
   template <int NIN, int NOUT, class Epi>
-  __device__ __noinline__ void xitem(int z, int y0, Epi& epi) {
+  __device__ __noinline__ void xitem(int z, int y0, Epi& epi_io) {
+    Epi epi = epi_io;                   // register copy of the epilogue
+    const int nx = this->nx, ny = this->ny, lgx = this->lgx, nkx = this->nkx, rb = this->rb;
+    const long long nspec = this->nspec;
+    C2<T>* const sm = this->sm;
+    C2<T>* const sm2 = this->sm2;
+    C2<T>* const S1 = this->S1;
+    const C2<T>* const twx = this->twx;
     const int npair = rb / 2;
     const long long off = (long long)z * nkx * ny + y0;
     C2<T>* X = sm;
@@ -93,6 +115,8 @@ struct Bulk {
     }
     __syncthreads();
     if constexpr (NOUT > 0) rows_forward_scatter<T, NOUT>(X, Y, S1 + off, nspec, ny, npair, lgpair, lgx, twx);
+    epi_io.acc = epi.acc;
+    epi_io.accmax = epi.accmax;
   }
   template <int NIN, int NOUT, class Epi>
   __device__ void xpass(Epi& epi, int slot) {
@@ -115,6 +139,19 @@ struct Bulk {
 
   // ---- y pass, forward: S1[c][z][kx][:] -> S2[c][kx][:][z] for z in [z0, z0 + zs) ----
   __device__ __noinline__ void yfwd() {
+    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
+    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
+    const long long nspec = this->nspec, ncell = this->ncell;
+    C2<T>* const sm = this->sm;
+    C2<T>* const sm2 = this->sm2;
+    C2<T>* const S1 = this->S1;
+    C2<T>* const S2 = this->S2;
+    const C2<T>* const twy = this->twy;
+    const C2<T>* const twz = this->twz;
+    const T* const ktab = this->ktab;
+    const T* const gtab = this->gtab;
+    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
+    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
     for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
@@ -139,6 +176,19 @@ struct Bulk {
   }
   // ---- y pass, inverse: S2 -> S1 ----
   __device__ __noinline__ void yinv() {
+    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
+    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
+    const long long nspec = this->nspec, ncell = this->ncell;
+    C2<T>* const sm = this->sm;
+    C2<T>* const sm2 = this->sm2;
+    C2<T>* const S1 = this->S1;
+    C2<T>* const S2 = this->S2;
+    const C2<T>* const twy = this->twy;
+    const C2<T>* const twz = this->twz;
+    const T* const ktab = this->ktab;
+    const T* const gtab = this->gtab;
+    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
+    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
     for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
@@ -167,6 +217,19 @@ struct Bulk {
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
   __device__ __noinline__ void zpass(int op) {
+    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
+    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
+    const long long nspec = this->nspec, ncell = this->ncell;
+    C2<T>* const sm = this->sm;
+    C2<T>* const sm2 = this->sm2;
+    C2<T>* const S1 = this->S1;
+    C2<T>* const S2 = this->S2;
+    const C2<T>* const twy = this->twy;
+    const C2<T>* const twz = this->twz;
+    const T* const ktab = this->ktab;
+    const T* const gtab = this->gtab;
+    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
+    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
@@ -231,12 +294,12 @@ struct Bulk {
 // ------------------------------------------------------------------------------------------
 template <typename T>
 struct BStage : EpiBase<T> {
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   StageIn in;
   __device__ void operator()(long long i, const T*, T* out) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long k = c * B->ncell + i;
+      const long long k = c * P.ncell + i;
       double v = in.y[k];
       for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][k];
       if (in.ynew) in.ynew[k] = v;
@@ -247,11 +310,11 @@ struct BStage : EpiBase<T> {
 
 template <typename T>
 struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law)
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   T n, e0, jc, rho_out;
   __device__ void operator()(long long i, const T* in, T* out) {
-    const int m = __ldg(&B->mask[i]);
-    const T jcl = B->jcmap ? __ldg(&B->jcmap[i]) : jc;
+    const int m = __ldg(&P.mask[i]);
+    const T jcl = P.jcmap ? __ldg(&P.jcmap[i]) : jc;
     const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
     out[0] = rho * in[0]; out[1] = rho * in[1]; out[2] = rho * in[2];
   }
@@ -259,17 +322,17 @@ struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law)
 
 template <typename T>
 struct BInit : EpiBase<T> {                // h_dot^0: h_dot_in on the conductor, warm or h_e_dot outside
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   bool warm;
   T hed[3];
   __device__ void operator()(long long i, const T* in, T* out) {
-    const bool cond = __ldg(&B->mask[i]) != 0;
+    const bool cond = __ldg(&P.mask[i]) != 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       T h;
       if (cond) h = in[c];                                 // -curl e (Eq. 14)
-      else h = warm ? B->hd[c * B->ncell + i] : hed[c];
-      B->hd[c * B->ncell + i] = h;
+      else h = warm ? P.hd[c * P.ncell + i] : hed[c];
+      P.hd[c * P.ncell + i] = h;
       out[c] = h;
     }
   }
@@ -277,40 +340,40 @@ struct BInit : EpiBase<T> {                // h_dot^0: h_dot_in on the conductor
 
 template <typename T>
 struct BMaskCond : EpiBase<T> {            // j_dot_in: keep on the conductor only
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   __device__ void operator()(long long i, const T* in, T* out) {
-    const bool cond = __ldg(&B->mask[i]) != 0;
+    const bool cond = __ldg(&P.mask[i]) != 0;
     out[0] = cond ? in[0] : (T)0; out[1] = cond ? in[1] : (T)0; out[2] = cond ? in[2] : (T)0;
   }
 };
 
 template <typename T>
 struct BUpdate : EpiBase<T> {              // Eq. 18 on free space, residual, forward
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   T hed[3];
   __device__ void operator()(long long i, const T* in, T* out) {
-    if (__ldg(&B->mask[i]) == 0) {
+    if (__ldg(&P.mask[i]) == 0) {
       double s2 = 0.0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T hn = hed[c] + in[c];
-        const T ho = B->hd[c * B->ncell + i];
+        const T ho = P.hd[c * P.ncell + i];
         const double df = (double)hn - (double)ho;
         s2 += df * df;
-        B->hd[c * B->ncell + i] = hn;
+        P.hd[c * P.ncell + i] = hn;
         out[c] = hn;
       }
       this->acc += sqrt(s2);
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[c] = B->hd[c * B->ncell + i];
+      for (int c = 0; c < 3; ++c) out[c] = P.hd[c * P.ncell + i];
     }
   }
 };
 
 template <typename T>
 struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 error contribution
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   double* kout;
   bool err;
   double h, rtol, atol;
@@ -318,8 +381,8 @@ struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 er
   __device__ void operator()(long long i, const T*, T*) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long k = c * B->ncell + i;
-      const double g = (double)B->hd[k];
+      const long long k = c * P.ncell + i;
+      const double g = (double)P.hd[k];
       kout[k] = g;
       if (err) {
         const double E = h * (-5.0 / 72.0 * k1[k] + 1.0 / 12.0 * k2[k] + 1.0 / 9.0 * k3[k] - 0.125 * g);
@@ -336,23 +399,23 @@ struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 er
 
 template <typename T>
 struct BStoreJ : EpiBase<T> {              // readout of j = curl h (FP64)
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   double* out;
   __device__ void operator()(long long i, const T* in, T*) {
-    out[i] = in[0]; out[B->ncell + i] = in[1]; out[2 * B->ncell + i] = in[2];
+    out[i] = in[0]; out[P.ncell + i] = in[1]; out[2 * P.ncell + i] = in[2];
   }
 };
 
 template <typename T>
 struct BMoment : EpiBase<T> {              // m = 1/2 sum dV r x j over the conductor, component `comp`
-  const Bulk<T>* B;
+  BulkPtrs<T> P;
   int comp;
   __device__ void operator()(long long i, const T* in, T*) {
-    if (__ldg(&B->mask[i]) == 0) return;
-    const int x = (int)(i % B->nx), y = (int)((i / B->nx) % B->ny), z = (int)(i / ((long long)B->nx * B->ny));
-    const double rx = -B->d.Lx + (x + 0.5) * B->d.dx;
-    const double ry = -B->d.Ly + (y + 0.5) * B->d.dy;
-    const double rz = -B->d.Lz + (z + 0.5) * B->d.dz;
+    if (__ldg(&P.mask[i]) == 0) return;
+    const int x = (int)(i % P.nx), y = (int)((i / P.nx) % P.ny), z = (int)(i / ((long long)P.nx * P.ny));
+    const double rx = -P.Lx + (x + 0.5) * P.dx;
+    const double ry = -P.Ly + (y + 0.5) * P.dy;
+    const double rz = -P.Lz + (z + 0.5) * P.dz;
     double v;
     if (comp == 0) v = ry * in[2] - rz * in[1];
     else if (comp == 1) v = rz * in[0] - rx * in[2];
@@ -376,17 +439,17 @@ __device__ __noinline__ RhsOut bulk_rhs(Bulk<T>& B, double t, int seg, const Sta
   const double hed_norm = sqrt(hed[0] * hed[0] + hed[1] * hed[1] + hed[2] * hed[2]);
 #define BSYNC(w) if (!B.sync(w)) { res.status = ST_BARRIER; return res; }
 #define BYZY(op, w) if (!B.yzy(op, w)) { res.status = ST_BARRIER; return res; }
-  { BStage<T> e; e.B = &B; e.in = sin; B.xpass<0, 3>(e, -1); }
+  { BStage<T> e; e.P = B.ptrs(); e.in = sin; B.xpass<0, 3>(e, -1); }
   BSYNC(101);
   BYZY(OP3_CURL, 102);                                                   // j = curl h
   {
-    BPower<T> e; e.B = &B; e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+    BPower<T> e; e.P = B.ptrs(); e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
     B.xpass<3, 3>(e, -1);                                                // e = rho j
   }
   BSYNC(105);
   BYZY(OP3_CURLNEG, 106);                                                // -curl e
   {
-    BInit<T> e; e.B = &B; e.warm = B.sh.warm_valid != 0;
+    BInit<T> e; e.P = B.ptrs(); e.warm = B.sh.warm_valid != 0;
     for (int c = 0; c < 3; ++c) e.hed[c] = (T)hed[c];
     B.xpass<3, 3>(e, -1);                                                // h_dot^0
   }
@@ -401,11 +464,11 @@ __device__ __noinline__ RhsOut bulk_rhs(Bulk<T>& B, double t, int seg, const Sta
   if (have_out) {
     for (; i < itmax; ++i) {
       BYZY(OP3_CURL, 110);                                               // j_dot = curl h_dot
-      { BMaskCond<T> e; e.B = &B; B.xpass<3, 3>(e, -1); }                // j_dot_in
+      { BMaskCond<T> e; e.P = B.ptrs(); B.xpass<3, 3>(e, -1); }                // j_dot_in
       BSYNC(113);
       BYZY(OP3_PHI, 114);                                                // Phi[j_dot_in]
       {
-        BUpdate<T> e; e.B = &B;
+        BUpdate<T> e; e.P = B.ptrs();
         for (int c = 0; c < 3; ++c) e.hed[c] = (T)hed[c];
         B.xpass<3, 3>(e, 0);                                             // Eq. 18
       }
@@ -418,9 +481,11 @@ __device__ __noinline__ RhsOut bulk_rhs(Bulk<T>& B, double t, int seg, const Sta
   res.iters = i;
   res.r = r;
   res.status = (!have_out || fixed || r < thresh) ? ST_OK : ST_NOCONV;
-  B.sh.warm_valid = 1;
+  // a call that failed with a residual above 1e3 times the threshold (or not finite) diverged:
+  // the next call starts cold
+  B.sh.warm_valid = (res.status == ST_NOCONV && !(r < 1e3 * thresh)) ? 0 : 1;
   {
-    BFinal<T> e; e.B = &B; e.kout = kout; e.is_max = true;
+    BFinal<T> e; e.P = B.ptrs(); e.kout = kout; e.is_max = true;
     e.err = want_err; e.h = h_err; e.rtol = d.rtol; e.atol = d.atol;
     e.k1 = e_k1; e.k2 = e_k2; e.k3 = e_k3; e.y = e_y; e.ynew = e_ynew;
     B.xpass<0, 0>(e, 3);
@@ -467,15 +532,15 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
     if (leader) { st->last_iters = r.iters; st->last_r = r.r; st->n_rhs += 1; st->n_iters += r.iters; }
   } else if (a.mode == MODE_J || a.mode == MODE_MOMENT) {
     StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
-    { BStage<T> e; e.B = &B; e.in = in; B.xpass<0, 3>(e, -1); }
+    { BStage<T> e; e.P = B.ptrs(); e.in = in; B.xpass<0, 3>(e, -1); }
     bool ok = B.sync(201) && B.yzy(OP3_CURL, 202);
     if (ok) {
       if (a.mode == MODE_J) {
-        BStoreJ<T> e; e.B = &B; e.out = a.out;
+        BStoreJ<T> e; e.P = B.ptrs(); e.out = a.out;
         B.xpass<3, 0>(e, -1);
       } else {
         for (int c = 0; c < 3 && ok; ++c) {
-          BMoment<T> e; e.B = &B; e.comp = c;
+          BMoment<T> e; e.P = B.ptrs(); e.comp = c;
           B.xpass<3, 0>(e, 4 + c);      // reads S1 only
           ok = B.sync(205 + c);
         }

@@ -550,8 +550,10 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   res.iters = i + 1;
   res.r = r;
   res.status = (!have_out || fixed || r < d.iter_tol) ? ST_OK : ST_NOCONV;
-  // warm start for the next call: h_dot stored, A still to subtract on free space
-  F.sh.warm_valid = 1;
+  // warm start for the next call: h_dot stored, A still to subtract on free space.  A call that
+  // failed with a residual above 1e3 tol (or not finite) diverged: the next call starts cold.
+  const bool diverged = res.status == ST_NOCONV && !(r < 1e3 * d.iter_tol);
+  F.sh.warm_valid = diverged ? 0 : 1;
   F.sh.A_prev = A;
 
   // finalize

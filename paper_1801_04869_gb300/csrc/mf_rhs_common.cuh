@@ -105,20 +105,26 @@ __device__ int bs23_advance(Rhs& R, const Desc& d, SolverState* st, const Kernel
       double* k3 = d.fbuf[ik3];
       double* k4 = d.fbuf[ik4];
       RhsOut r;
+      r.status = ST_OK;
+      r.r = 0.0;
       if (!k1_valid) {
+        // a k1 whose outside iteration did not converge rejects the attempt like any other
+        // stage; the warm start keeps the progress, so the next attempt continues from it
         StageIn in{y, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
         r = R(t, seg, in, k1, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
         ++n_rhs; n_it += r.iters; it[0] = r.iters;
-        if (r.status != ST_OK) { status = r.status == ST_BARRIER ? ST_BARRIER : ST_NOCONV; break; }
-        if (r.nonfinite) { status = ST_NONFINITE; break; }
-        k1_valid = 1;
+        if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+        if (r.status == ST_OK && r.nonfinite) { status = ST_NONFINITE; break; }
+        if (r.status == ST_OK) k1_valid = 1;
       }
       int outcome = 1;
       double err = INFINITY;
-      StageIn s2{y, 1, {0.5 * h, 0, 0}, {k1, nullptr, nullptr}, nullptr};
-      r = R(t + 0.5 * h, seg, s2, k2, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
-      ++n_rhs; n_it += r.iters; it[1] = r.iters;
-      if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+      if (r.status == ST_OK) {
+        StageIn s2{y, 1, {0.5 * h, 0, 0}, {k1, nullptr, nullptr}, nullptr};
+        r = R(t + 0.5 * h, seg, s2, k2, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+        ++n_rhs; n_it += r.iters; it[1] = r.iters;
+        if (r.status == ST_BARRIER) { status = ST_BARRIER; break; }
+      }
       if (r.status == ST_OK) {
         StageIn s3{y, 1, {0.75 * h, 0, 0}, {k2, nullptr, nullptr}, nullptr};
         r = R(t + 0.75 * h, seg, s3, k3, 0, false, 0, nullptr, nullptr, nullptr, nullptr, nullptr);

@@ -96,3 +96,21 @@ def test_adaptive_controller_and_knot_clipping():
     nxt = [e for e in s.log if e.outcome == ACCEPT][i + 1]
     assert nxt.iters[0] >= 0                        # k1 recomputed after the slope jump
     assert all(e.err <= 1.0 for e in s.log if e.outcome == ACCEPT)
+
+
+def test_failed_first_stage_is_retried_with_half_step():
+    # a right-hand side whose outside iteration fails on its first two calls: the attempts are
+    # rejected (h halved) and k1 is evaluated again each time, as for any failed stage
+    calls = {"n": 0}
+
+    def rhs(t, y, seg, force):
+        calls["n"] += 1
+        return -y, 1, (3 if calls["n"] <= 2 else 0)
+
+    s = BS23(rhs, Waveform((0.0,), (0.0,)), rtol=1e-6, atol=1e-6, h0=0.1)
+    s.start(0.0, np.array([1.0]), 1.0)
+    s.advance(0.3)
+    assert [e.outcome for e in s.log[:2]] == [2, 2]
+    assert s.log[0].iters[0] >= 0 and s.log[1].iters[0] >= 0 and s.log[2].iters[0] >= 0
+    assert s.log[1].h == pytest.approx(0.05) and s.log[2].h == pytest.approx(0.025)
+    assert s.y[0] == pytest.approx(math.exp(-0.3), rel=1e-5)
