@@ -73,10 +73,9 @@ struct Bulk {
     while (p2 * 2 <= P) p2 *= 2;
     P = p2;
     nblocks = gridDim.x;
-    wq.base = 0;
   }
 
-  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed); }
 
   __device__ BulkPtrs<T> ptrs() const {
     return BulkPtrs<T>{mask, jcmap, hd, ncell, nx, ny, d.Lx, d.Ly, d.Lz, d.dx, d.dy, d.dz};
@@ -122,7 +121,7 @@ struct Bulk {
   __device__ void xpass(Epi& epi, int slot) {
     const int per_z = ny / rb;
     const int nitems = per_z * nz;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
@@ -131,7 +130,6 @@ struct Bulk {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
-    wq.end_phase();
   }
   __device__ double total(int slot, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, (ny / rb) * nz, is_max, sh.red);
@@ -154,11 +152,11 @@ struct Bulk {
     (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       gather_batched<T, 4>(sm, S1, nl << lgy,
-          [&](int e) {
+          [=](int e) {
             const int l = e >> lgy, y = e & (ny - 1);
             const int c = l / zs, dz = l - c * zs;
             return c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y;
@@ -172,7 +170,6 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase();
   }
   // ---- y pass, inverse: S2 -> S1 ----
   __device__ __noinline__ void yinv() {
@@ -191,16 +188,16 @@ struct Bulk {
     (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       gather_batched<T, 4>(sm, S2, nl << lgy,
-          [&](int e) {
+          [=](int e) {
             const int dz = e % zs, rest = e / zs;
             const int ky = rest & (ny - 1), c = rest >> lgy;
             return c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz;
           },
-          [&](int e) {
+          [=](int e) {
             const int dz = e % zs, rest = e / zs;
             const int ky = rest & (ny - 1), c = rest >> lgy;
             return ((c * zs + dz) << lgy) + ky;
@@ -213,7 +210,6 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase();
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
   __device__ __noinline__ void zpass(int op) {
@@ -233,12 +229,12 @@ struct Bulk {
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       const int kx = it / per_kx, ky0 = (it % per_kx) * P;
       const long long base = ((long long)kx * ny + ky0) * nz;
       const int pl = P << lgz;                       // values per component
       gather_batched<T, 4>(sm, S2, 3 * pl,
-          [&](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
+          [=](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
           [](int e) { return e; });
       C2<T>* X = fft_lines<T, -1>(sm, sm2, lgz, 3 * P, twz);
       C2<T>* Y = X == sm ? sm2 : sm;
@@ -275,7 +271,6 @@ struct Bulk {
       }
       __syncthreads();
     }
-    wq.end_phase();
   }
 
   // Yf, Z(op), Yi with barriers; the x passes before and after are separate
@@ -348,17 +343,17 @@ struct BMaskCond : EpiBase<T> {            // j_dot_in: keep on the conductor on
 };
 
 template <typename T>
-struct BUpdate : EpiBase<T> {              // Eq. 18 on free space, residual, forward
+struct BUpdate : EpiBase<T, T> {           // Eq. 18 on free space, residual, forward
   BulkPtrs<T> P;
   T hed[3];
   __device__ void operator()(long long i, const T* in, T* out) {
     if (__ldg(&P.mask[i]) == 0) {
-      double s2 = 0.0;
+      T s2 = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T hn = hed[c] + in[c];
         const T ho = P.hd[c * P.ncell + i];
-        const double df = (double)hn - (double)ho;
+        const T df = hn - ho;
         s2 += df * df;
         P.hd[c * P.ncell + i] = hn;
         out[c] = hn;
@@ -517,6 +512,7 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
   SolverState* st = d.st;
   if (threadIdx.x == 0) {
     sh.warm_valid = st->warm_valid;
+    sh.bar_passed = 0;
     sh.A_prev = 0.0;
   }
   __syncthreads();

@@ -76,47 +76,29 @@ struct SolverState {
   double pad[4];
 };
 
-// The arrival counter, the generation word that waiting CTAs poll, and the work counter of the
-// dynamic schedule sit on separate 128-byte lines so that polling does not slow the atomics.
+// Barrier state of one launch (zeroed before every launch).  `count` is a monotonic arrival
+// counter: the k-th barrier of the launch is passed once it reaches k * grid.  Bit 63 is the
+// abort flag, so one polled word carries both.
+constexpr unsigned long long BARRIER_ABORT = 1ull << 63;
 struct alignas(128) GridBarrier {
-  unsigned int count;
-  int abort;
-  int where;
+  unsigned long long count;
+  int where;                     // site number of the barrier whose wait timed out
   unsigned int pad0[29];
-  unsigned int gen;
-  unsigned int pad1[31];
-  unsigned long long work;       // work-item counter of the dynamic schedule (monotonic)
-  unsigned long long pad2[15];
 };
 
-// Dynamic schedule of the work items of one phase.  CTA b first takes item b (no atomic);
-// when a phase has more items than CTAs, the rest come from a monotonic counter, item =
-// grid + counter - base, and every CTA ends with exactly one failed grab, so the counter
-// advances by (n - grid) + grid in every CTA's view; `base` tracks that without a reset.
-// Phases that use the schedule must be separated by a grid barrier.
+// Static round-robin schedule of the work items of one phase: CTA b takes items b, b + grid,
+// b + 2 grid, ...  The items of a phase are uniform, so a fixed assignment balances as well as
+// a dynamic one and needs no atomic between items.
 struct WorkQueue {
-  unsigned long long base;
-  int nitems, first;
+  int nitems, cur;
   __device__ __forceinline__ int begin(int n) {
     nitems = n;
-    first = 1;
-    return (int)blockIdx.x < n ? (int)blockIdx.x : n;
+    cur = (int)blockIdx.x;
+    return cur < n ? cur : n;
   }
-  // next item after the current one (>= nitems: done).  A negative counter value would mean
-  // a CTA grabbed ahead of the others; it raises the abort flag instead of touching memory.
-  __device__ __forceinline__ int next(GridBarrier* gb, int* s_item) {
-    if (nitems <= (int)gridDim.x) return nitems;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      long long v = (long long)(atomicAdd(&gb->work, 1ull) - base) + gridDim.x;
-      if (v < (long long)gridDim.x) { atomicExch(&gb->abort, 1); v = 0x7fffffff; }
-      *s_item = v > 0x7fffffff ? 0x7fffffff : (int)v;
-    }
-    __syncthreads();
-    return *s_item;
-  }
-  __device__ __forceinline__ void end_phase() {
-    if (nitems > (int)gridDim.x) base += (unsigned long long)nitems;   // (n - grid) + grid
+  __device__ __forceinline__ int next() {
+    cur += (int)gridDim.x;
+    return cur < nitems ? cur : nitems;
   }
 };
 
@@ -175,48 +157,46 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ int ld_volatile_i32(const int* p) {
-  return *(const volatile int*)p;
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // 4 s per barrier
 
-// returns false when the launch must stop (abort raised)
-__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks, int where) {
+// Returns false when the launch must stop (abort raised).  `passed` counts the barriers this
+// CTA has passed in the launch (shared memory, written by thread 0 only, zero at launch).
+// Arrival is a fire-and-forget release add after the CTA barrier; the wait polls the same word
+// with acquire loads.
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks, int where,
+                                          unsigned long long* passed) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned int my_gen = ld_acquire_u32(&gb->gen);
-    __threadfence();
-    unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      unsigned long long t0 = globaltimer_ns();
+    const unsigned long long target = (*passed + 1) * nblocks;
+    *passed += 1;
+    red_release_add_u64(&gb->count, 1ull);
+    unsigned long long v = ld_acquire_u64(&gb->count);
+    if ((v & ~BARRIER_ABORT) < target && !(v & BARRIER_ABORT)) {
+      const unsigned long long t0 = globaltimer_ns();
       unsigned int nap = 32;
-      while (ld_acquire_u32(&gb->gen) == my_gen) {
-        if (ld_volatile_i32(&gb->abort)) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
-          atomicExch(&gb->abort, 1);
-          atomicExch(&gb->where, where);
-          ok = 0;
-          break;
-        }
+      do {
         __nanosleep(nap);
         if (nap < 128) nap <<= 1;
-      }
+        if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
+          atomicOr(&gb->count, BARRIER_ABORT);
+          atomicExch(&gb->where, where);
+          v |= BARRIER_ABORT;
+          break;
+        }
+        v = ld_acquire_u64(&gb->count);
+      } while ((v & ~BARRIER_ABORT) < target && !(v & BARRIER_ABORT));
     }
-    __threadfence();
-    if (ld_volatile_i32(&gb->abort)) ok = 0;
-    s_ok = ok;
+    s_ok = (v & BARRIER_ABORT) ? 0 : 1;
   }
   __syncthreads();
   return s_ok != 0;

@@ -135,7 +135,7 @@ __device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines
   C2<T>* in = a;
   C2<T>* out = b;
   while (rem > 0) {
-    if (sizeof(T) == 4 && rem >= 4 && rem != 5) {
+    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) {
       // single precision: radix 16 (three shared-memory passes for 2048 points)
       fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw + off);
       off += 15 << lgp; lgp += 4; rem -= 4;
@@ -165,21 +165,26 @@ __device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines
 // global memory directly (both in natural order, coalesced), so the round trip costs m + 1
 // shared-memory exchanges instead of 2m + 3.
 // ------------------------------------------------------------------------------------------
+// The plan is packed into one integer (4 bits per stage) so that it stays in registers when a
+// stage is selected by a run-time index.
 struct FftPlan {
   int m;
-  int lgr[8];
+  unsigned packed;
+  __device__ __forceinline__ int lgr(int s) const { return (int)((packed >> (4 * s)) & 15u); }
 };
 template <typename T>
 __device__ __forceinline__ FftPlan fft_plan(int lgL) {
   FftPlan P;
   P.m = 0;
+  P.packed = 0;
   int rem = lgL;
   while (rem > 0) {
     int l;
-    if (sizeof(T) == 4 && rem >= 4 && rem != 5) l = 4;
+    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) l = 4;
     else if (rem >= 3) l = 3;
     else l = rem;
-    P.lgr[P.m++] = l;
+    P.packed |= (unsigned)l << (4 * P.m);
+    ++P.m;
     rem -= l;
   }
   return P;
@@ -289,54 +294,57 @@ template <typename T, int NFI, int NFO, class Src, class Dst, class Mul, class A
 __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T>* __restrict__ tw,
                                Src gsrc, Dst gdst, Mul mul, AfterFirst after_first) {
   const FftPlan P = fft_plan<T>(lgL);
-  // block offsets in table A (plan order) and table B (reversed plan, right after A)
-  int offA[8], offB[8];
+  const int m = P.m;
+  // blocks of the stage-ordered tables: table A (plan order) starts at 0, table B (reversed
+  // plan) right after A; both offsets advance as the stages run
   int lenA = 0;
   {
     int lgp = 0;
-    for (int s = 0; s < P.m; ++s) { offA[s] = lenA; lenA += ((1 << P.lgr[s]) - 1) << lgp; lgp += P.lgr[s]; }
-    int lenB = lenA, lgq = 0;
-    for (int s = 0; s < P.m; ++s) {
-      const int l = P.lgr[P.m - 1 - s];
-      offB[s] = lenB; lenB += ((1 << l) - 1) << lgq; lgq += l;
-    }
+    for (int s = 0; s < m; ++s) { lenA += ((1 << P.lgr(s)) - 1) << lgp; lgp += P.lgr(s); }
   }
+  int offA = 0;
   int lgp = 0;
   // forward stage 0: source -> sa
-  fft_stage_io_any<T, -1>(P.lgr[0], lgL, 0, NFI * nl, tw + offA[0],
+  const int l0 = P.lgr(0);
+  fft_stage_io_any<T, -1>(l0, lgL, 0, NFI * nl, tw + offA,
       [=](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
       [=](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
   after_first();                     // the source of the first stage is no longer needed
-  lgp += P.lgr[0];
+  offA += ((1 << l0) - 1) << lgp;
+  lgp += l0;
   C2<T>* cur = sa;
   C2<T>* oth = sb;
-  for (int s = 1; s < P.m - 1; ++s) {
-    const int lgr = P.lgr[s];
-    const C2<T>* t = tw + offA[s];
+  for (int s = 1; s < m - 1; ++s) {
+    const int lgr = P.lgr(s);
+    const C2<T>* t = tw + offA;
     if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, -1>(cur, oth, lgL, lgp, NFI * nl, t);
     else if (lgr == 3) fft_stage<T, 8, 3, -1>(cur, oth, lgL, lgp, NFI * nl, t);
     else if (lgr == 2) fft_stage<T, 4, 2, -1>(cur, oth, lgL, lgp, NFI * nl, t);
     else fft_stage<T, 2, 1, -1>(cur, oth, lgL, lgp, NFI * nl, t);
+    offA += ((1 << lgr) - 1) << lgp;
     lgp += lgr;
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // forward last stage + multiplier + inverse first stage (p = 1: no twiddles)
-  fft_middle_any<T, NFI, NFO>(P.lgr[P.m - 1], cur, oth, lgL, nl, tw + offA[P.m - 1], mul);
+  const int lm = P.lgr(m - 1);
+  fft_middle_any<T, NFI, NFO>(lm, cur, oth, lgL, nl, tw + offA, mul);
   { C2<T>* tt = cur; cur = oth; oth = tt; }
-  int lgpi = P.lgr[P.m - 1];
-  for (int s = P.m - 2; s >= 1; --s) {
-    const int lgr = P.lgr[s];
-    const C2<T>* t = tw + offB[P.m - 1 - s];
+  int offB = lenA + ((1 << lm) - 1);  // table B block of the inverse stage after the fused one
+  int lgpi = lm;
+  for (int s = m - 2; s >= 1; --s) {
+    const int lgr = P.lgr(s);
+    const C2<T>* t = tw + offB;
     if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
     else if (lgr == 3) fft_stage<T, 8, 3, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
     else if (lgr == 2) fft_stage<T, 4, 2, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
     else fft_stage<T, 2, 1, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
+    offB += ((1 << lgr) - 1) << lgpi;
     lgpi += lgr;
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // inverse last stage: shared -> destination
   const C2<T>* const last = cur;
-  fft_stage_io_any<T, +1>(P.lgr[0], lgL, lgpi, NFO * nl, tw + offB[P.m - 1],
+  fft_stage_io_any<T, +1>(l0, lgL, lgpi, NFO * nl, tw + offB,
       [=](int line, int pos) { return last[sp((line << lgL) + pos)]; },
       [=](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
 }

@@ -56,7 +56,7 @@ struct Film {
   const T* gtab;     // Gaussian factors, same layout
   int rb1, rb2;      // rows per item for one- and two-field row passes
   unsigned nblocks;
-  WorkQueue wq;      // dynamic schedule of the work items
+  WorkQueue wq;      // schedule of the work items
 
   __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
     nx = d.nx; ny = d.ny; lgx = d.lgx; lgy = d.lgy; half = nx / 2; nkx = half + 1;
@@ -72,10 +72,9 @@ struct Film {
     rb1 = d.rows_per_item;
     rb2 = d.zs_per_item;
     nblocks = gridDim.x;
-    wq.base = 0;
   }
 
-  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where); }
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed); }
 
   __device__ FilmPtrs<T> ptrs() const { return FilmPtrs<T>{mask, jcmap, hd, u, q1, q2, nx}; }
 
@@ -133,7 +132,7 @@ struct Film {
       return;
     }
     gather_batched<T, 4>(sm, Sin, (nin * nl) << lgy,
-        [&](int e) {
+        [=](int e) {
           const int j = e >> lgy, f = j / nl, l = j - f * nl;
           return f * nspec + (long long)(kx0 + l) * ny + (e & (ny - 1));
         },
@@ -188,11 +187,10 @@ struct Film {
   __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
     const int nl = col_lines(nin > nout ? nin : nout);
     const int nitems = (nkx + nl - 1) / nl;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       const int kx0 = it * nl;
       col_item(kx0, kx0 + nl <= nkx ? nl : nkx - kx0, Sin, nin, Sout, nout, op);
     }
-    wq.end_phase();
   }
 
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
@@ -245,7 +243,7 @@ struct Film {
   template <int NIN, int NOUT, class Epi>
   __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
     const int nitems = ny / rb;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next(d.gb, &sh.item)) {
+    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
@@ -254,7 +252,6 @@ struct Film {
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
     }
-    wq.end_phase();
   }
   __device__ double total(int slot, int rb, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, ny / rb, is_max, sh.red);
@@ -281,7 +278,7 @@ struct EpiStage : EpiBase<T> {
     }
     if (in.ynew) st4(in.ynew + i, v);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { this->acc += v.v[q]; out[0].v[q] = (T)v.v[q]; }
+    for (int q = 0; q < 4; ++q) out[0].v[q] = (T)v.v[q];
   }
 };
 
@@ -340,7 +337,7 @@ struct EpiPower : EpiBase<T> {
 
 // P5: initial h_dot (warm start), sum over D
 template <typename T>
-struct EpiInit : EpiBase<T> {
+struct EpiInit : EpiBase<T, T> {
   FilmPtrs<T> P;
   bool warm;
   T A_prev, hed;
@@ -353,7 +350,7 @@ struct EpiInit : EpiBase<T> {
     for (int q = 0; q < 4; ++q) {
       if (mask_at(m, q) != 0) h.v[q] = in[0].v[q];             // h_dot_in on the conductor
       else h.v[q] = warm ? w.v[q] - A_prev : hed;             // warm start (Section 2.2)
-      this->acc += (double)h.v[q];
+      this->acc += h.v[q];
     }
     st4(P.hd + i, h);
     out[0] = h;
@@ -362,7 +359,7 @@ struct EpiInit : EpiBase<T> {
 
 // P7: u = raw - A q1; sum over free space; forward of mask_out u
 template <typename T>
-struct EpiU : EpiBase<T> {
+struct EpiU : EpiBase<T, T> {
   FilmPtrs<T> P;
   T A;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
@@ -373,7 +370,7 @@ struct EpiU : EpiBase<T> {
     for (int q = 0; q < 4; ++q) {
       v.v[q] = in[0].v[q] - A * q1.v[q];
       const bool o = mask_at(m, q) == 0;
-      if (o) this->acc += (double)v.v[q];
+      if (o) this->acc += v.v[q];
       out[0].v[q] = o ? v.v[q] : (T)0;
     }
     st4(P.u + i, v);
@@ -382,21 +379,21 @@ struct EpiU : EpiBase<T> {
 
 // P8: residual sum over free space of |u - C|
 template <typename T>
-struct EpiResid : EpiBase<T> {
+struct EpiResid : EpiBase<T, T> {
   FilmPtrs<T> P;
-  double C;
+  T C;
   __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
     const uchar4 m = ldmask4(P.mask + i);
     const V4<T> u = ld4(P.u + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (mask_at(m, q) == 0) this->acc += fabs((double)u.v[q] - C);
+      if (mask_at(m, q) == 0) this->acc += fabs(u.v[q] - C);
   }
 };
 
 // P10: h_dot update on free space (Eq. 12), sum over D, forward
 template <typename T>
-struct EpiUpdate : EpiBase<T> {
+struct EpiUpdate : EpiBase<T, T> {
   FilmPtrs<T> P;
   T A, C;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
@@ -409,7 +406,7 @@ struct EpiUpdate : EpiBase<T> {
         const T w = in[0].v[q] - C * q2.v[q];
         h.v[q] = (h.v[q] - A) - w;
       }
-      this->acc += (double)h.v[q];
+      this->acc += h.v[q];
     }
     st4(P.hd + i, h);
     out[0] = h;
@@ -518,22 +515,23 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     if (!have_out) { C = 0.0; r = 0.0; break; }
     C = F.total(1, F.rb1) / nout;                                       // Eq. 11
     {
-      // P8 (residual, row items) and P9 (K2 column items) share one phase and one item space
-      EpiResid<T> e; e.P = F.ptrs(); e.C = C;
+      // P9 (K2 column items, the longer ones, first) and P8 (residual, row items) share one
+      // phase and one item space
+      EpiResid<T> e; e.P = F.ptrs(); e.C = (T)C;
       const int nl9 = F.col_lines(1);
       const int n8 = F.ny / F.rb1, n9 = (F.nkx + nl9 - 1) / nl9;
-      for (int it = F.wq.begin(n8 + n9); it < n8 + n9; it = F.wq.next(d.gb, &F.sh.item)) {
-        if (it < n8) {
-          e.acc = 0.0;
-          F.template row_item<0, 0>(it * F.rb1, F.rb1, nullptr, nullptr, e);
-          const double v = block_sum(e.acc, F.sh.red);
-          if (threadIdx.x == 0) d.partials[(size_t)2 * d.max_items + it] = v;
-        } else {
-          const int kx0 = (it - n8) * nl9;
+      for (int it = F.wq.begin(n8 + n9); it < n8 + n9; it = F.wq.next()) {
+        if (it < n9) {
+          const int kx0 = it * nl9;
           F.col_item(kx0, kx0 + nl9 <= F.nkx ? nl9 : F.nkx - kx0, F.Sb, 1, F.Sb, 1, OP_K2);
+        } else {
+          const int r8 = it - n9;
+          e.acc = 0.0;
+          F.template row_item<0, 0>(r8 * F.rb1, F.rb1, nullptr, nullptr, e);
+          const double v = block_sum(e.acc, F.sh.red);
+          if (threadIdx.x == 0) d.partials[(size_t)2 * d.max_items + r8] = v;
         }
       }
-      F.wq.end_phase();
     }
     if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
     r = F.total(2, F.rb1) / nout;
@@ -592,6 +590,7 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
   SolverState* st = d.st;
   if (threadIdx.x == 0) {
     sh.warm_valid = st->warm_valid;
+    sh.bar_passed = 0;
     sh.A_prev = st->A_prev;
   }
   __syncthreads();

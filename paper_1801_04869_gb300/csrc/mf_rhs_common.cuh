@@ -19,10 +19,10 @@ struct StageIn {
 // per-CTA copy of the scalars every CTA agrees on
 struct Shared {
   double red[NT / 32];
-  int item;                      // broadcast slot of the dynamic schedule
   double A, C, r, hed;
   int warm_valid;
   double A_prev;
+  unsigned long long bar_passed;  // grid barriers passed in this launch (thread 0)
 };
 
 // ------------------------------------------------------------------------------------------
@@ -58,9 +58,13 @@ __device__ __forceinline__ double he_next_knot(const Desc& d, double t) {
   return INFINITY;
 }
 
-template <typename T>
+// Acc is the type of the per-thread partial sums: the transform precision T in the epilogues of
+// the outside iteration (FP64 arithmetic runs at a small fraction of the FP32 rate on this part),
+// double where a sum feeds the integrator's error norm or a readout.  The partials of a CTA
+// are combined in double.
+template <typename T, typename Acc = double>
 struct EpiBase {
-  double acc = 0.0, accmax = 0.0;
+  Acc acc = 0, accmax = 0;
   bool is_max = false;
 };
 

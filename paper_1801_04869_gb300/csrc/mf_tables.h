@@ -11,13 +11,15 @@
 #pragma once
 #include <cmath>
 
+#include "mf_common.cuh"
+
 namespace mf {
 
 inline int plan_lgr(int lgL, bool single, int* lgr) {
   int m = 0, rem = lgL;
   while (rem > 0) {
     int l;
-    if (single && rem >= 4 && rem != 5) l = 4;
+    if (single && VPT >= 16 && rem >= 4 && rem != 5) l = 4;
     else if (rem >= 3) l = 3;
     else l = rem;
     lgr[m++] = l;
