@@ -36,7 +36,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t Sa, Sb, hd, u, q1, q2, jc, mask, twx, twy, twz, ktab, gtab, fbuf[6], partials, st, gb,
-      log, knots, mscr, total;
+      log, knots, mscr, desc, total;
   long long ncell, nspec, nstate;
   int max_items;
 };
@@ -97,6 +97,7 @@ Layout layout(const mf_params* p) {
   L.log = take(LOG_CAP * sizeof(StepLog));
   L.knots = take(2 * (size_t)(p->he_knots > 0 ? p->he_knots : 1) * 8);
   L.mscr = take(8 * 8);
+  L.desc = take(sizeof(Desc));
   L.total = o;
   return L;
 }
@@ -248,6 +249,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   d.he_t = (const double*)(w + L.knots);
   d.he_v = d.he_t + (p->he_knots > 0 ? p->he_knots : 1);
   pb->scratch_m = (double*)(w + L.mscr);
+  d.dev = (const Desc*)(w + L.desc);
 
   // launch configuration: all CTAs co-resident, no more than the widest pass can use
   const size_t smem = kernel_smem_bytes(d);
@@ -329,6 +331,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   cp(w + L.gtab, gt.data(), gt.size());
   cp(w + L.knots, knots.data(), knots.size() * 8);
   cp(w + L.st, &s0, sizeof(s0));
+  cp(w + L.desc, &d, sizeof(Desc));     // the kernels read the descriptor from here
   if (e == cudaSuccess) e = cudaMemsetAsync(w + L.fbuf[0], 0, L.nstate * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w + L.hd, 0, (p->dim == 2 ? 1 : 3) * L.ncell * ts, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // host staging buffers die below

@@ -50,7 +50,6 @@ struct Bulk {
   const T* ktab; const T* gtab;     // kx (nkx), ky (ny), kz (nz)
   int rb, zs, P;
   unsigned nblocks;
-  WorkQueue wq;
 
   __device__ Bulk(const Desc& dd, C2<T>* s, Shared& shr)
       : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
@@ -121,7 +120,7 @@ struct Bulk {
   __device__ void xpass(Epi& epi, int slot) {
     const int per_z = ny / rb;
     const int nitems = per_z * nz;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
@@ -152,7 +151,7 @@ struct Bulk {
     (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       gather_batched<T, 4>(sm, S1, nl << lgy,
@@ -188,7 +187,7 @@ struct Bulk {
     (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
     const int nitems = nkx * per_kx;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       const int kx = it / per_kx, z0 = (it % per_kx) * zs;
       const int nl = 3 * zs;
       gather_batched<T, 4>(sm, S2, nl << lgy,
@@ -229,7 +228,7 @@ struct Bulk {
     const int per_kx = ny / P;
     const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       const int kx = it / per_kx, ky0 = (it % per_kx) * P;
       const long long base = ((long long)kx * ny + ky0) * nz;
       const int pl = P << lgz;                       // values per component
@@ -505,18 +504,22 @@ struct BulkRhs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) bulk_kernel(Desc d, KernelArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C2<T>* sm = (C2<T>*)smraw;
+__global__ void __launch_bounds__(NT, 2) bulk_kernel(const Desc* __restrict__ dg, KernelArgs a) {
+  C2<T>* sm = dsm<T>();
   __shared__ Shared sh;
+  // one copy of the pass object per CTA, in shared memory: its members are read as broadcasts
+  // instead of per-thread local-memory copies
+  __shared__ __align__(16) unsigned char objraw[sizeof(Bulk<T>)];
+  const Desc& d = *dg;
   SolverState* st = d.st;
   if (threadIdx.x == 0) {
     sh.warm_valid = st->warm_valid;
     sh.bar_passed = 0;
     sh.A_prev = 0.0;
   }
+  if (threadIdx.x == 0) new (objraw) Bulk<T>(d, sm, sh);
   __syncthreads();
-  Bulk<T> B(d, sm, sh);
+  Bulk<T>& B = *reinterpret_cast<Bulk<T>*>(objraw);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int status = ST_OK;
 
@@ -572,9 +575,9 @@ int bulk_max_blocks(int precision, size_t smem) {
 }
 
 cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s) {
-  Desc dd = d;
+  const Desc* dg = d.dev;
   KernelArgs aa = a;
-  void* args[] = {&dd, &aa};
+  void* args[] = {&dg, &aa};
   const size_t smem = kernel_smem_bytes(d);
   const void* fn = precision ? (const void*)bulk_kernel<float> : (const void*)bulk_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);

@@ -17,6 +17,11 @@ constexpr int BATCH = NT * VPT;   // complex points one CTA transforms at once (
 __host__ __device__ __forceinline__ constexpr int sp(int e) { return e + (e >> 4); }
 constexpr int BATCH_PAD = BATCH + BATCH / 16;
 
+// The dynamic shared memory of the persistent kernels: two FFT buffers of BATCH_PAD complex
+// values each.  Passes address it by element offset from this base, so that every access is a
+// shared-memory access with 32-bit index arithmetic.
+extern __shared__ __align__(16) unsigned char mf_dsmem[];
+
 // ------------------------------------------------------------------------------------------
 // complex numbers
 // ------------------------------------------------------------------------------------------
@@ -33,6 +38,10 @@ template <typename T> __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) { re
 template <typename T> __device__ __forceinline__ C2<T> cmul_si(C2<T> a, int s) {
   return s > 0 ? C2<T>{-a.y, a.x} : C2<T>{a.y, -a.x};
 }
+
+template <typename T> __device__ __forceinline__ C2<T>* dsm() { return reinterpret_cast<C2<T>*>(mf_dsmem); }
+// element offset of a pointer into the dynamic shared memory
+template <typename T> __device__ __forceinline__ int dsm_off(const C2<T>* p) { return (int)(p - dsm<T>()); }
 
 // read-only (non-coherent) load of a complex value
 __device__ __forceinline__ C2<float> ldg_c2(const C2<float>* p) {
@@ -86,21 +95,6 @@ struct alignas(128) GridBarrier {
   unsigned int pad0[29];
 };
 
-// Static round-robin schedule of the work items of one phase: CTA b takes items b, b + grid,
-// b + 2 grid, ...  The items of a phase are uniform, so a fixed assignment balances as well as
-// a dynamic one and needs no atomic between items.
-struct WorkQueue {
-  int nitems, cur;
-  __device__ __forceinline__ int begin(int n) {
-    nitems = n;
-    cur = (int)blockIdx.x;
-    return cur < n ? cur : n;
-  }
-  __device__ __forceinline__ int next() {
-    cur += (int)gridDim.x;
-    return cur < nitems ? cur : nitems;
-  }
-};
 
 // ------------------------------------------------------------------------------------------
 // problem descriptor (kernel argument, plain data)
@@ -145,6 +139,7 @@ struct Desc {
   int rows_per_item;             // 2D row pass / 3D x pass rows per work item (even)
   int zs_per_item;               // 3D y pass z-lines per work item
   int grid;                      // CTAs of the persistent launch
+  const struct Desc* dev;        // device copy of this descriptor (what the kernels read)
 };
 
 // ------------------------------------------------------------------------------------------

@@ -92,33 +92,55 @@ __device__ __forceinline__ void dft(C2<T>* v) {
 // w^(j k) with k = i mod p and w = exp(DIR 2 pi i / (p R)), and writes its length-R DFT to
 // out[(i - k) R + k + j p].  `tw` is the stage's block of the stage-ordered table: entry
 // (j - 1) p + k holds w^(j k) for the forward direction.
+//
+// Padded addressing: for a stride s that is a multiple of 16, sp(e + j s) = sp(e) + j (s + s/16),
+// so a butterfly's R elements sit at one base plus multiples of a padded stride.  The same
+// holds with stride 1 when e is a multiple of R (R divides 16): the R outputs of a p = 1 stage
+// share one padding group.  Other strides (short lines) take sp() per element.
 template <typename T, int R, int LGR, int DIR>
-__device__ __forceinline__ void fft_stage(const C2<T>* in, C2<T>* out, int lgL, int lgp, int nlines,
+__device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int lgL, int lgp, int nlines,
                                           const C2<T>* __restrict__ tw) {
+  C2<T>* const S = dsm<T>();
+  const int in = dsm_off(in_p), out = dsm_off(out_p);
   const int lgq = lgL - LGR;          // log2(L / R)
   const int q = 1 << lgq;
   const int p = 1 << lgp;
   const int nb = nlines << lgq;       // butterflies in this stage
+  const int qs = q + (q >> 4), ps = p + (p >> 4);
+  const bool fast_in = lgq >= 4, fast_out = lgp == 0 || lgp >= 4;
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int line = b >> lgq, i = b & (q - 1);
     const int k = i & (p - 1);
     const int src = (line << lgL) + i;
     C2<T> v[R];
+    if (fast_in) {
+      const int a0 = in + sp(src);
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = in[sp(src + (j << lgq))];
+      for (int j = 0; j < R; ++j) v[j] = S[a0 + j * qs];
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
+    }
     if (lgp > 0) {
       // w^(j k) from the stage's block of the stage-ordered table (conjugated for DIR > 0)
+      const C2<T>* __restrict__ twk = tw + k;
 #pragma unroll
       for (int j = 1; j < R; ++j) {
-        C2<T> w = ldg_c2(tw + (((j - 1) << lgp) + k));
+        C2<T> w = ldg_c2(twk + (j - 1) * p);
         if (DIR > 0) w.y = -w.y;
         v[j] = cmul(v[j], w);
       }
     }
     dft<T, R, DIR>(v);
     const int dst = (line << lgL) + ((i - k) << LGR) + k;
+    if (fast_out) {
+      const int a0 = out + sp(dst);
 #pragma unroll
-    for (int j = 0; j < R; ++j) out[sp(dst + (j << lgp))] = v[j];
+      for (int j = 0; j < R; ++j) S[a0 + j * ps] = v[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) S[out + sp(dst + (j << lgp))] = v[j];
+    }
   }
   __syncthreads();
 }
@@ -190,24 +212,57 @@ __device__ __forceinline__ FftPlan fft_plan(int lgL) {
   return P;
 }
 
-// one stage with arbitrary element I/O: ld(line, pos) -> C2<T>, st(line, pos, value)
-template <typename T, int R, int LGR, int DIR, class Ld, class St>
-__device__ __forceinline__ void fft_stage_io(int lgL, int lgp, int nlines, const C2<T>* __restrict__ tw,
-                                             Ld ld, St st) {
+// First stage of a transform (p = 1, no twiddles) reading its input through ld(line, pos) (global
+// memory) and writing shared buffer `out`.
+template <typename T, int R, int LGR, int DIR, class Ld>
+__device__ __forceinline__ void fft_first_io(int lgL, int nlines, Ld ld, C2<T>* out_p) {
+  C2<T>* const S = dsm<T>();
+  const int out = dsm_off(out_p);
+  const int lgq = lgL - LGR;
+  const int q = 1 << lgq;
+  const int nb = nlines << lgq;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int line = b >> lgq, i = b & (q - 1);
+    C2<T> v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = ld(line, i + (j << lgq));
+    dft<T, R, DIR>(v);
+    const int a0 = out + sp((line << lgL) + (i << LGR));     // a multiple of R: one padding group
+#pragma unroll
+    for (int j = 0; j < R; ++j) S[a0 + j] = v[j];
+  }
+  __syncthreads();
+}
+// Last stage of a transform reading shared buffer `in` and writing through st(line, pos, v)
+// (global memory).
+template <typename T, int R, int LGR, int DIR, class St>
+__device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp, int nlines,
+                                            const C2<T>* __restrict__ tw, St st) {
+  C2<T>* const S = dsm<T>();
+  const int in = dsm_off(in_p);
   const int lgq = lgL - LGR;
   const int q = 1 << lgq;
   const int p = 1 << lgp;
   const int nb = nlines << lgq;
+  const int qs = q + (q >> 4);
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int line = b >> lgq, i = b & (q - 1);
     const int k = i & (p - 1);
+    const int src = (line << lgL) + i;
     C2<T> v[R];
+    if (lgq >= 4) {
+      const int a0 = in + sp(src);
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = ld(line, i + (j << lgq));
+      for (int j = 0; j < R; ++j) v[j] = S[a0 + j * qs];
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
+    }
     if (lgp > 0) {
+      const C2<T>* __restrict__ twk = tw + k;
 #pragma unroll
       for (int j = 1; j < R; ++j) {
-        C2<T> w = ldg_c2(tw + (((j - 1) << lgp) + k));
+        C2<T> w = ldg_c2(twk + (j - 1) * p);
         if (DIR > 0) w.y = -w.y;
         v[j] = cmul(v[j], w);
       }
@@ -220,34 +275,52 @@ __device__ __forceinline__ void fft_stage_io(int lgL, int lgp, int nlines, const
   __syncthreads();
 }
 
-template <typename T, int DIR, class Ld, class St>
-__device__ __forceinline__ void fft_stage_io_any(int lgr, int lgL, int lgp, int nlines,
-                                                 const C2<T>* __restrict__ tw, Ld ld, St st) {
+template <typename T, int DIR, class Ld>
+__device__ __forceinline__ void fft_first_io_any(int lgr, int lgL, int nlines, Ld ld, C2<T>* out) {
   if constexpr (sizeof(T) == 4) {
-    if (lgr == 4) { fft_stage_io<T, 16, 4, DIR>(lgL, lgp, nlines, tw, ld, st); return; }
+    if (lgr == 4) { fft_first_io<T, 16, 4, DIR>(lgL, nlines, ld, out); return; }
   }
-  if (lgr == 3) fft_stage_io<T, 8, 3, DIR>(lgL, lgp, nlines, tw, ld, st);
-  else if (lgr == 2) fft_stage_io<T, 4, 2, DIR>(lgL, lgp, nlines, tw, ld, st);
-  else fft_stage_io<T, 2, 1, DIR>(lgL, lgp, nlines, tw, ld, st);
+  if (lgr == 3) fft_first_io<T, 8, 3, DIR>(lgL, nlines, ld, out);
+  else if (lgr == 2) fft_first_io<T, 4, 2, DIR>(lgL, nlines, ld, out);
+  else fft_first_io<T, 2, 1, DIR>(lgL, nlines, ld, out);
+}
+template <typename T, int DIR, class St>
+__device__ __forceinline__ void fft_last_io_any(int lgr, const C2<T>* in, int lgL, int lgp, int nlines,
+                                                const C2<T>* __restrict__ tw, St st) {
+  if constexpr (sizeof(T) == 4) {
+    if (lgr == 4) { fft_last_io<T, 16, 4, DIR>(in, lgL, lgp, nlines, tw, st); return; }
+  }
+  if (lgr == 3) fft_last_io<T, 8, 3, DIR>(in, lgL, lgp, nlines, tw, st);
+  else if (lgr == 2) fft_last_io<T, 4, 2, DIR>(in, lgL, lgp, nlines, tw, st);
+  else fft_last_io<T, 2, 1, DIR>(in, lgL, lgp, nlines, tw, st);
 }
 
 // the fused middle pass: forward last stage (radix R) on NFI input fields, mul(l, pos, x[], y[])
 // per position, inverse first stage on NFO output fields.  Shared line f * nl + l holds field
 // f of line group l.
 template <typename T, int R, int LGR, int NFI, int NFO, class Mul>
-__device__ __forceinline__ void fft_middle(const C2<T>* in, C2<T>* out, int lgL, int nl,
+__device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int lgL, int nl,
                                            const C2<T>* __restrict__ tw, Mul mul) {
+  C2<T>* const S = dsm<T>();
+  const int in = dsm_off(in_p), out = dsm_off(out_p);
   const int lgq = lgL - LGR;
   const int q = 1 << lgq;
   const int nb = nl << lgq;
+  const int qs = q + (q >> 4);
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int l = b >> lgq, i = b & (q - 1);
     C2<T> x[NFI][R];
 #pragma unroll
     for (int f = 0; f < NFI; ++f) {
       const int base = ((f * nl + l) << lgL) + i;
+      if (lgq >= 4) {
+        const int a0 = in + sp(base);
 #pragma unroll
-      for (int j = 0; j < R; ++j) x[f][j] = in[sp(base + (j << lgq))];
+        for (int j = 0; j < R; ++j) x[f][j] = S[a0 + j * qs];
+      } else {
+#pragma unroll
+        for (int j = 0; j < R; ++j) x[f][j] = S[in + sp(base + (j << lgq))];
+      }
       // twiddles of the last forward stage (p = q, k = i), from its block of the table
 #pragma unroll
       for (int j = 1; j < R; ++j)
@@ -267,9 +340,9 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in, C2<T>* out, int lgL,
 #pragma unroll
     for (int g = 0; g < NFO; ++g) {
       dft<T, R, +1>(y[g]);
-      const int base = ((g * nl + l) << lgL) + (i << LGR);
+      const int a0 = out + sp(((g * nl + l) << lgL) + (i << LGR));   // a multiple of R
 #pragma unroll
-      for (int j = 0; j < R; ++j) out[sp(base + j)] = y[g][j];
+      for (int j = 0; j < R; ++j) S[a0 + j] = y[g][j];
     }
   }
   __syncthreads();
@@ -306,9 +379,8 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
   int lgp = 0;
   // forward stage 0: source -> sa
   const int l0 = P.lgr(0);
-  fft_stage_io_any<T, -1>(l0, lgL, 0, NFI * nl, tw + offA,
-      [=](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; },
-      [=](int line, int pos, C2<T> v) { sa[sp((line << lgL) + pos)] = v; });
+  fft_first_io_any<T, -1>(l0, lgL, NFI * nl,
+      [=](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; }, sa);
   after_first();                     // the source of the first stage is no longer needed
   offA += ((1 << l0) - 1) << lgp;
   lgp += l0;
@@ -343,9 +415,7 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // inverse last stage: shared -> destination
-  const C2<T>* const last = cur;
-  fft_stage_io_any<T, +1>(l0, lgL, lgpi, NFO * nl, tw + offB,
-      [=](int line, int pos) { return last[sp((line << lgL) + pos)]; },
+  fft_last_io_any<T, +1>(l0, cur, lgL, lgpi, NFO * nl, tw + offB,
       [=](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
 }
 

@@ -56,7 +56,6 @@ struct Film {
   const T* gtab;     // Gaussian factors, same layout
   int rb1, rb2;      // rows per item for one- and two-field row passes
   unsigned nblocks;
-  WorkQueue wq;      // schedule of the work items
 
   __device__ Film(const Desc& dd, C2<T>* s, Shared& shr) : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
     nx = d.nx; ny = d.ny; lgx = d.lgx; lgy = d.lgy; half = nx / 2; nkx = half + 1;
@@ -187,7 +186,7 @@ struct Film {
   __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
     const int nl = col_lines(nin > nout ? nin : nout);
     const int nitems = (nkx + nl - 1) / nl;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       const int kx0 = it * nl;
       col_item(kx0, kx0 + nl <= nkx ? nl : nkx - kx0, Sin, nin, Sout, nout, op);
     }
@@ -209,8 +208,10 @@ struct Film {
     const int lgpair = __ffs(npair) - 1;
     if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(smA, smB, Sin + y0, nspec, ny, npair, lgpair, lgx, twx);
     C2<T>* Y = X == smA ? smB : smA;
+    C2<T>* const S = dsm<T>();
+    const int ix = dsm_off(X);
     // four consecutive cells of both rows of a pair per step; the epilogue issues its global
-    // loads for the four cells together
+    // loads for the four cells together (x0 is a multiple of 4: one padding group)
     const int lgq = lgx - 2;
 #pragma unroll 2
     for (int e = threadIdx.x; e < (npair << lgq); e += NT) {
@@ -220,7 +221,7 @@ struct Film {
       for (int f = 0; f < NIN; ++f) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const C2<T> z = X[sp(((f * npair + pr) << lgx) + x0 + j)];
+          const C2<T> z = S[ix + sp(((f * npair + pr) << lgx) + x0) + j];
           ina[f].v[j] = z.x; inb[f].v[j] = z.y;
         }
       }
@@ -230,7 +231,7 @@ struct Film {
 #pragma unroll
       for (int f = 0; f < NOUT; ++f) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) X[sp(((f * npair + pr) << lgx) + x0 + j)] = C2<T>{oa[f].v[j], ob[f].v[j]};
+        for (int j = 0; j < 4; ++j) S[ix + sp(((f * npair + pr) << lgx) + x0) + j] = C2<T>{oa[f].v[j], ob[f].v[j]};
       }
     }
     __syncthreads();
@@ -243,7 +244,7 @@ struct Film {
   template <int NIN, int NOUT, class Epi>
   __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
     const int nitems = ny / rb;
-    for (int it = wq.begin(nitems); it < nitems; it = wq.next()) {
+    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
       row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
@@ -520,7 +521,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
       EpiResid<T> e; e.P = F.ptrs(); e.C = (T)C;
       const int nl9 = F.col_lines(1);
       const int n8 = F.ny / F.rb1, n9 = (F.nkx + nl9 - 1) / nl9;
-      for (int it = F.wq.begin(n8 + n9); it < n8 + n9; it = F.wq.next()) {
+      for (int it = (int)blockIdx.x; it < n8 + n9; it += (int)gridDim.x) {
         if (it < n9) {
           const int kx0 = it * nl9;
           F.col_item(kx0, kx0 + nl9 <= F.nkx ? nl9 : F.nkx - kx0, F.Sb, 1, F.Sb, 1, OP_K2);
@@ -583,18 +584,22 @@ struct FilmRhs {
 // the persistent kernel
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NT, 2) film_kernel(Desc d, KernelArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C2<T>* sm = (C2<T>*)smraw;
+__global__ void __launch_bounds__(NT, 2) film_kernel(const Desc* __restrict__ dg, KernelArgs a) {
+  C2<T>* sm = dsm<T>();
   __shared__ Shared sh;
+  // one copy of the pass object per CTA, in shared memory: its members are read as broadcasts
+  // instead of per-thread local-memory copies
+  __shared__ __align__(16) unsigned char objraw[sizeof(Film<T>)];
+  const Desc& d = *dg;
   SolverState* st = d.st;
   if (threadIdx.x == 0) {
     sh.warm_valid = st->warm_valid;
     sh.bar_passed = 0;
     sh.A_prev = st->A_prev;
   }
+  if (threadIdx.x == 0) new (objraw) Film<T>(d, sm, sh);
   __syncthreads();
-  Film<T> F(d, sm, sh);
+  Film<T>& F = *reinterpret_cast<Film<T>*>(objraw);
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   int status = ST_OK;
 
@@ -663,9 +668,9 @@ int film_max_blocks(int precision, size_t smem) {
 }
 
 cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s) {
-  Desc dd = d;
+  const Desc* dg = d.dev;
   KernelArgs aa = a;
-  void* args[] = {&dd, &aa};
+  void* args[] = {&dg, &aa};
   const size_t smem = kernel_smem_bytes(d);
   const void* fn = precision ? (const void*)film_kernel<float> : (const void*)film_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);

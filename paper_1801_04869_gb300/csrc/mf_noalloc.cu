@@ -97,6 +97,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   const size_t okt = take(nk * ts), ogt = take(nk * ts);
   const size_t opart = take((size_t)8 * ny * 8), ost = take(sizeof(SolverState)), ogb = take(sizeof(GridBarrier));
   const size_t oknots = take(2 * (size_t)(p->he_knots > 0 ? p->he_knots : 1) * 8);
+  const size_t odesc = take(sizeof(Desc));
   if (o > NOALLOC_BYTES) {
     set_err(err, err_len, "static scratch too small for these parameters");
     return MF_ERR_WORKSPACE;
@@ -131,6 +132,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   d.st = (SolverState*)(w + ost); d.gb = (GridBarrier*)(w + ogb);
   d.he_t = (const double*)(w + oknots);
   d.he_v = d.he_t + (p->he_knots > 0 ? p->he_knots : 1);
+  d.dev = (const Desc*)(w + odesc);
 
   d.nz = 1;
   const size_t smem = kernel_smem_bytes(d);
@@ -215,6 +217,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   SolverState s0;
   std::memset(&s0, 0, sizeof(s0));
   copy_sync(w + ost, &s0, sizeof(s0));
+  copy_sync(w + odesc, &d, sizeof(Desc));   // the kernel reads the descriptor from here
   if (e != cudaSuccess) { set_err(err, err_len, cudaGetErrorString(e)); return MF_ERR_CUDA; }
 
   KernelArgs a;

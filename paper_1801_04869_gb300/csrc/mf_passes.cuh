@@ -27,6 +27,8 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
                                                       int npair, int lgpair, int lgx,
                                                       const C2<T>* __restrict__ twx) {
   constexpr int U = 2;
+  C2<T>* const S = dsm<T>();
+  const int ia = dsm_off(sm);
   const int nx = 1 << lgx, half = nx >> 1;
   const int per_f = npair * (half + 1);
   const int total = NIN * per_f;
@@ -52,10 +54,10 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
         const C2<T> A = v[u].a, B = v[u].b;
         const int z0 = (f * npair + pr) << lgx;
         if (k == 0 || k == half) {
-          sm[sp(z0 + k)] = C2<T>{A.x, B.x};
+          S[ia + sp(z0 + k)] = C2<T>{A.x, B.x};
         } else {
-          sm[sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
-          sm[sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
+          S[ia + sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
+          S[ia + sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
         }
       }
     }
@@ -73,13 +75,15 @@ __device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C
                                                      const C2<T>* __restrict__ twx) {
   const int nx = 1 << lgx, half = nx >> 1;
   const C2<T>* sm = fft_lines<T, -1>(sm_in, sm2, lgx, NOUT * npair, twx);
+  C2<T>* const S = dsm<T>();
+  const int io = dsm_off(sm);
   const int per_f = npair * (half + 1);
   for (int e = threadIdx.x; e < NOUT * per_f; e += NT) {
     const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
     const int rest = e - f * per_f;
     const int k = rest >> lgpair, pr = rest & (npair - 1);
     const int z0 = (f * npair + pr) << lgx;
-    const C2<T> zk = sm[sp(z0 + k)], zm = sm[sp(z0 + ((nx - k) & (nx - 1)))];
+    const C2<T> zk = S[io + sp(z0 + k)], zm = S[io + sp(z0 + ((nx - k) & (nx - 1)))];
     const T hh = (T)0.5;
     CPair<T> o;
     o.a = C2<T>{hh * (zk.x + zm.x), hh * (zk.y - zm.y)};

@@ -1,6 +1,8 @@
 // Pieces shared by the film (2D) and bulk (3D) right-hand sides: the applied field h_e(t),
 // the stage input of the integrator, per-CTA scalars and epilogue/result records.
 #pragma once
+#include <new>
+
 #include "mf_passes.cuh"
 
 namespace mf {
