@@ -237,12 +237,12 @@ struct Bulk {
           [](int e) { return e; });
       C2<T>* X = fft_lines<T, -1>(sm, sm2, lgz, 3 * P, twz);
       C2<T>* Y = X == sm ? sm2 : sm;
-      const T kxv = ktab[kx], gx = gtab[kx];
+      const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
       const T kxo = kx == half ? (T)0 : kxv;
       for (int e = threadIdx.x; e < pl; e += NT) {
         const int p = e >> lgz, kz = e & (nz - 1);
         const int ky = ky0 + p;
-        const T kyv = ktab[nkx + ky], kzv = ktab[nkx + ny + kz];
+        const T kyv = ldg_tab(&ktab[nkx + ky]), kzv = ldg_tab(&ktab[nkx + ny + kz]);
         const T kyo = ky == ny / 2 ? (T)0 : kyv;
         const T kzo = kz == nz / 2 ? (T)0 : kzv;
         const C2<T> a = X[sp(e)], b = X[sp(pl + e)], c = X[sp(2 * pl + e)];
@@ -255,7 +255,7 @@ struct Bulk {
           const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
           f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
         } else {
-          const T G = gx * gtab[nkx + ky] * gtab[nkx + ny + kz];
+          const T G = gx * ldg_tab(&gtab[nkx + ky]) * ldg_tab(&gtab[nkx + ny + kz]);
           f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
         }
         X[sp(e)] = cmul_si(cscale(cx, f), 1);

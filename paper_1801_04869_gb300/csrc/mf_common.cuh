@@ -43,13 +43,38 @@ template <typename T> __device__ __forceinline__ C2<T>* dsm() { return reinterpr
 // element offset of a pointer into the dynamic shared memory
 template <typename T> __device__ __forceinline__ int dsm_off(const C2<T>* p) { return (int)(p - dsm<T>()); }
 
-// read-only (non-coherent) load of a complex value
+// Loads with L1 placement hints.  Tables (twiddles, wavenumbers) are read over and over and
+// should stay in L1 (evict_last); field data streams through once per pass and should not
+// displace them (no_allocate).  ldg_* use the read-only path and are only for data that no
+// thread writes during the launch; lds_* are coherent loads for data written by earlier phases.
 __device__ __forceinline__ C2<float> ldg_c2(const C2<float>* p) {
-  const float2 v = __ldg((const float2*)p);
+  float2 v;
+  asm volatile("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
   return {v.x, v.y};
 }
 __device__ __forceinline__ C2<double> ldg_c2(const C2<double>* p) {
-  const double2 v = __ldg((const double2*)p);
+  double2 v;
+  asm volatile("ld.global.nc.L1::evict_last.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ float ldg_tab(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ldg_tab(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ C2<float> lds_c2(const C2<float>* p) {
+  float2 v;
+  asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+  return {v.x, v.y};
+}
+__device__ __forceinline__ C2<double> lds_c2(const C2<double>* p) {
+  double2 v;
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p) : "memory");
   return {v.x, v.y};
 }
 

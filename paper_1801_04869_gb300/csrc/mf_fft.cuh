@@ -87,6 +87,25 @@ __device__ __forceinline__ void dft(C2<T>* v) {
   }
 }
 
+// Twiddles w^(j k), 1 <= j < R, of one butterfly: the entries j = 1, 2, 4, 8 come from the
+// stage's block of the stage-ordered table (entry (j - 1) p + k), the others are products of
+// two of them (w^(3k) = w^k w^(2k), ...), at most three roundings from the table values.
+// Conjugated for the inverse direction.
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void stage_twiddles(const C2<T>* __restrict__ twk, int p, C2<T>* w) {
+#pragma unroll
+  for (int j = 1; j < R; j <<= 1) {
+    w[j] = ldg_c2(twk + (j - 1) * p);
+    if (DIR > 0) w[j].y = -w[j].y;
+  }
+#pragma unroll
+  for (int j = 3; j < R; ++j) {
+    if ((j & (j - 1)) == 0) continue;
+    const int hb = j >= 8 ? 8 : (j >= 4 ? 4 : 2);          // highest power of two below j
+    w[j] = cmul(w[hb], w[j - hb]);
+  }
+}
+
 // one Stockham stage of radix R from `in` to `out`; p = 2^lgp = product of the radices
 // already applied.  Butterfly b of line `line` reads in[i + j L/R] (j < R), multiplies by
 // w^(j k) with k = i mod p and w = exp(DIR 2 pi i / (p R)), and writes its length-R DFT to
@@ -122,14 +141,10 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int l
       for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
     }
     if (lgp > 0) {
-      // w^(j k) from the stage's block of the stage-ordered table (conjugated for DIR > 0)
-      const C2<T>* __restrict__ twk = tw + k;
+      C2<T> w[R];
+      stage_twiddles<T, R, DIR>(tw + k, p, w);
 #pragma unroll
-      for (int j = 1; j < R; ++j) {
-        C2<T> w = ldg_c2(twk + (j - 1) * p);
-        if (DIR > 0) w.y = -w.y;
-        v[j] = cmul(v[j], w);
-      }
+      for (int j = 1; j < R; ++j) v[j] = cmul(v[j], w[j]);
     }
     dft<T, R, DIR>(v);
     const int dst = (line << lgL) + ((i - k) << LGR) + k;
@@ -259,13 +274,10 @@ __device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp,
       for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
     }
     if (lgp > 0) {
-      const C2<T>* __restrict__ twk = tw + k;
+      C2<T> w[R];
+      stage_twiddles<T, R, DIR>(tw + k, p, w);
 #pragma unroll
-      for (int j = 1; j < R; ++j) {
-        C2<T> w = ldg_c2(twk + (j - 1) * p);
-        if (DIR > 0) w.y = -w.y;
-        v[j] = cmul(v[j], w);
-      }
+      for (int j = 1; j < R; ++j) v[j] = cmul(v[j], w[j]);
     }
     dft<T, R, DIR>(v);
     const int dpos = ((i - k) << LGR) + k;
@@ -310,6 +322,9 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int 
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int l = b >> lgq, i = b & (q - 1);
     C2<T> x[NFI][R];
+    // twiddles of the last forward stage (p = q, k = i), from its block of the table
+    C2<T> w[R];
+    stage_twiddles<T, R, -1>(tw + i, q, w);
 #pragma unroll
     for (int f = 0; f < NFI; ++f) {
       const int base = ((f * nl + l) << lgL) + i;
@@ -321,10 +336,8 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int 
 #pragma unroll
         for (int j = 0; j < R; ++j) x[f][j] = S[in + sp(base + (j << lgq))];
       }
-      // twiddles of the last forward stage (p = q, k = i), from its block of the table
 #pragma unroll
-      for (int j = 1; j < R; ++j)
-        x[f][j] = cmul(x[f][j], ldg_c2(tw + (((j - 1) << lgq) + i)));
+      for (int j = 1; j < R; ++j) x[f][j] = cmul(x[f][j], w[j]);
       dft<T, R, -1>(x[f]);
     }
     C2<T> y[NFO][R];
@@ -380,7 +393,7 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
   // forward stage 0: source -> sa
   const int l0 = P.lgr(0);
   fft_first_io_any<T, -1>(l0, lgL, NFI * nl,
-      [=](int line, int pos) { const int f = line / nl; return gsrc(f, line - f * nl)[pos]; }, sa);
+      [=](int line, int pos) { const int f = line / nl; return lds_c2(gsrc(f, line - f * nl) + pos); }, sa);
   after_first();                     // the source of the first stage is no longer needed
   offA += ((1 << l0) - 1) << lgp;
   lgp += l0;

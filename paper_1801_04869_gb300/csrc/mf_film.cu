@@ -94,11 +94,11 @@ struct Film {
       const T s = (T)1 / (T)ncell;
       auto coef = [=](int l, int ky, T& kxo, T& kyo, T& k2, T& G) {
         const int kx = kx0 + l;
-        const T kxv = __ldg(&ktab[kx]), kyv = __ldg(&ktab[nkx + ky]);
+        const T kxv = ldg_tab(&ktab[kx]), kyv = ldg_tab(&ktab[nkx + ky]);
         kxo = (kx == half) ? (T)0 : kxv;
         kyo = (ky == ny / 2) ? (T)0 : kyv;
         k2 = kxv * kxv + kyv * kyv;
-        G = __ldg(&gtab[kx]) * __ldg(&gtab[nkx + ky]);
+        G = ldg_tab(&gtab[kx]) * ldg_tab(&gtab[nkx + ky]);
       };
       if (op == OP_GRAD) {
         fft_round_trip<T, 1, 2>(sm, sm2, lgy, nl, twy, src, dst,
@@ -142,9 +142,9 @@ struct Film {
     for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
       const int l = e >> lgy, ky = e & (ny - 1);
       const int kx = kx0 + l;
-      const T kxv = __ldg(&ktab[kx]), gx = __ldg(&gtab[kx]);
+      const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
       const T kxo = (kx == half) ? (T)0 : kxv;
-      const T kyv = __ldg(&ktab[nkx + ky]), G = gx * __ldg(&gtab[nkx + ky]);
+      const T kyv = ldg_tab(&ktab[nkx + ky]), G = gx * ldg_tab(&gtab[nkx + ky]);
       const T kyo = (ky == ny / 2) ? (T)0 : kyv;
       const T k2 = kxv * kxv + kyv * kyv;
       const int i0 = (0 * nl + l) * ny + ky, i1 = (1 * nl + l) * ny + ky;

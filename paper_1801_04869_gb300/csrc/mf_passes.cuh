@@ -16,6 +16,20 @@ namespace mf {
 // Two adjacent complex values (one pair of rows at one x-wavenumber) moved as one vector.
 template <typename T> struct alignas(2 * sizeof(C2<T>)) CPair { C2<T> a, b; };
 
+// Two adjacent complex values from global memory, not kept in L1 (streamed once per pass).
+__device__ __forceinline__ CPair<float> ld_pair_stream(const C2<float>* p) {
+  CPair<float> v;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.a.x), "=f"(v.a.y), "=f"(v.b.x), "=f"(v.b.y) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
+  CPair<double> v;
+  v.a = lds_c2(p);
+  v.b = lds_c2(p + 1);
+  return v;
+}
+
 // Gather the half spectra of rows [2 pr, 2 pr + 1] of NIN fields from global memory into
 // packed complex lines of length nx in shared buffer `sm`, then inverse-transform them along
 // x (second buffer `sm2`).  Returns the buffer holding the rows (row 2pr in .x, 2pr+1 in .y).
@@ -41,7 +55,7 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
         const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
         const int rest = e - f * per_f;
         const int k = rest >> lgpair, pr = rest & (npair - 1);
-        v[u] = *(const CPair<T>*)(src + f * fstride + (long long)k * kstride + 2 * pr);
+        v[u] = ld_pair_stream(src + f * fstride + (long long)k * kstride + 2 * pr);
       }
     }
 #pragma unroll
@@ -134,7 +148,7 @@ __device__ __forceinline__ void gather_batched(C2<T>* sm, const C2<T>* src, int 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * NT;
-      if (e < total) v[u] = src[goff(e)];
+      if (e < total) v[u] = lds_c2(src + goff(e));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -150,22 +164,31 @@ __device__ __forceinline__ void gather_batched(C2<T>* sm, const C2<T>* src, int 
 // four consecutive cells: vector loads and stores (index a multiple of 4, 16-byte aligned)
 // ------------------------------------------------------------------------------------------
 template <typename T> struct V4 { T v[4]; };
+// field loads of the epilogues stream through once per pass: not kept in L1
 __device__ __forceinline__ V4<float> ld4(const float* p) {
-  const float4 a = *(const float4*)p;
-  return {{a.x, a.y, a.z, a.w}};
+  V4<float> r;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p) : "memory");
+  return r;
 }
 __device__ __forceinline__ V4<double> ld4(const double* p) {
-  const double2 a = ((const double2*)p)[0], b = ((const double2*)p)[1];
-  return {{a.x, a.y, b.x, b.y}};
+  V4<double> r;
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p) : "memory");
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[2]), "=d"(r.v[3]) : "l"(p + 2) : "memory");
+  return r;
 }
 // read-only for the whole launch (non-coherent path)
 __device__ __forceinline__ V4<float> ldg4(const float* p) {
-  const float4 a = __ldg((const float4*)p);
-  return {{a.x, a.y, a.z, a.w}};
+  V4<float> r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p));
+  return r;
 }
 __device__ __forceinline__ V4<double> ldg4(const double* p) {
-  const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);
-  return {{a.x, a.y, b.x, b.y}};
+  V4<double> r;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[2]), "=d"(r.v[3]) : "l"(p + 2));
+  return r;
 }
 __device__ __forceinline__ void st4(float* p, const V4<float>& v) {
   *(float4*)p = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
@@ -174,7 +197,11 @@ __device__ __forceinline__ void st4(double* p, const V4<double>& v) {
   ((double2*)p)[0] = make_double2(v.v[0], v.v[1]);
   ((double2*)p)[1] = make_double2(v.v[2], v.v[3]);
 }
-__device__ __forceinline__ uchar4 ldmask4(const uint8_t* p) { return __ldg((const uchar4*)p); }
+__device__ __forceinline__ uchar4 ldmask4(const uint8_t* p) {
+  unsigned int w;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(w) : "l"(p));
+  return make_uchar4(w & 255u, (w >> 8) & 255u, (w >> 16) & 255u, w >> 24);
+}
 __device__ __forceinline__ int mask_at(const uchar4& m, int j) {
   return j == 0 ? m.x : (j == 1 ? m.y : (j == 2 ? m.z : m.w));
 }
