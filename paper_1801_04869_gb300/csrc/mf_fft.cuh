@@ -160,35 +160,43 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int l
   __syncthreads();
 }
 
-// FFT of nlines lines of length 2^lgL held in shared buffer `a`, using `b` as the second
-// buffer of the autosort; returns the buffer that holds the result (a or b).  Must be called
-// by all NT threads of the CTA (it synchronises).
+// Stages `first` .. m-1 of the FFT of nlines lines of length 2^lgL held in shared buffer `a`
+// (`b` is the second buffer of the autosort); returns the buffer that holds the result.  With
+// first = 1 the caller has done stage 0 itself (fft_first_io).  Must be called by all NT
+// threads of the CTA (it synchronises).
 template <typename T, int DIR>
-__device__ __noinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines,
-                                         const C2<T>* __restrict__ tw) {
+__device__ __noinline__ C2<T>* fft_lines_from(C2<T>* a, C2<T>* b, int lgL, int nlines,
+                                              const C2<T>* __restrict__ tw, int first) {
   int lgp = 0;
   int rem = lgL;
   int off = 0;                       // block of the current stage in the stage-ordered table
   C2<T>* in = a;
   C2<T>* out = b;
-  while (rem > 0) {
-    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) {
-      // single precision: radix 16 (three shared-memory passes for 2048 points)
-      fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      off += 15 << lgp; lgp += 4; rem -= 4;
-    } else if (rem >= 3) {
-      fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      off += 7 << lgp; lgp += 3; rem -= 3;
-    } else if (rem == 2) {
-      fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      off += 3 << lgp; lgp += 2; rem -= 2;
-    } else {
-      fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      off += 1 << lgp; lgp += 1; rem -= 1;
+  for (int stage = 0; rem > 0; ++stage) {
+    int l;
+    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) l = 4;
+    else if (rem >= 3) l = 3;
+    else l = rem;
+    if (stage >= first) {
+      if (sizeof(T) == 4 && l == 4) fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      else if (l == 3) fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      else if (l == 2) fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      else fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      C2<T>* t = in; in = out; out = t;
     }
-    C2<T>* t = in; in = out; out = t;
+    off += ((1 << l) - 1) << lgp;
+    lgp += l;
+    rem -= l;
   }
   return in;
+}
+// FFT of nlines lines of length 2^lgL held in shared buffer `a`, using `b` as the second
+// buffer of the autosort; returns the buffer that holds the result (a or b).  Must be called
+// by all NT threads of the CTA (it synchronises).
+template <typename T, int DIR>
+__device__ __forceinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines,
+                                            const C2<T>* __restrict__ tw) {
+  return fft_lines_from<T, DIR>(a, b, lgL, nlines, tw, 0);
 }
 
 // ------------------------------------------------------------------------------------------

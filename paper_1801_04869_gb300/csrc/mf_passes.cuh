@@ -30,54 +30,32 @@ __device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
   return v;
 }
 
-// Gather the half spectra of rows [2 pr, 2 pr + 1] of NIN fields from global memory into
-// packed complex lines of length nx in shared buffer `sm`, then inverse-transform them along
-// x (second buffer `sm2`).  Returns the buffer holding the rows (row 2pr in .x, 2pr+1 in .y).
-// Global element (f, kx, row r) lives at src + f * fstride + kx * kstride + r; each thread
-// issues U independent vector loads before it writes shared memory.
+// Inverse-transform along x the half spectra of rows [2 pr, 2 pr + 1] of NIN fields, packed
+// as complex lines a + i b (Hermitian symmetry of real rows): returns the shared buffer (sm or
+// sm2) holding the rows, row 2pr in .x and row 2pr+1 in .y.  Global element (f, kx, row r)
+// lives at src + f * fstride + kx * kstride + r.  The first transform stage reads its inputs
+// straight from global memory, all of a butterfly's loads in flight together: position m of
+// a packed line is A[m] + i B[m] for m <= nx/2 and conj(A[nx-m]) + i conj(B[nx-m]) above,
+// with the imaginary parts of the real DC and Nyquist terms dropped.
 template <typename T, int NIN>
 __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, const C2<T>* src,
                                                       long long fstride, long long kstride,
                                                       int npair, int lgpair, int lgx,
                                                       const C2<T>* __restrict__ twx) {
-  constexpr int U = 2;
-  C2<T>* const S = dsm<T>();
-  const int ia = dsm_off(sm);
   const int nx = 1 << lgx, half = nx >> 1;
-  const int per_f = npair * (half + 1);
-  const int total = NIN * per_f;
-  for (int e0 = threadIdx.x; e0 < total; e0 += NT * U) {
-    CPair<T> v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * NT;
-      if (e < total) {
-        const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
-        const int rest = e - f * per_f;
-        const int k = rest >> lgpair, pr = rest & (npair - 1);
-        v[u] = ld_pair_stream(src + f * fstride + (long long)k * kstride + 2 * pr);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * NT;
-      if (e < total) {
-        const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
-        const int rest = e - f * per_f;
-        const int k = rest >> lgpair, pr = rest & (npair - 1);
-        const C2<T> A = v[u].a, B = v[u].b;
-        const int z0 = (f * npair + pr) << lgx;
-        if (k == 0 || k == half) {
-          S[ia + sp(z0 + k)] = C2<T>{A.x, B.x};
-        } else {
-          S[ia + sp(z0 + k)] = C2<T>{A.x - B.y, A.y + B.x};          // A + i B
-          S[ia + sp(z0 + nx - k)] = C2<T>{A.x + B.y, B.x - A.y};     // conj(A) + i conj(B)
-        }
-      }
-    }
-  }
-  __syncthreads();
-  return fft_lines<T, +1>(sm, sm2, lgx, NIN * npair, twx);
+  auto ld = [=](int line, int m) -> C2<T> {
+    const int f = line >> lgpair, pr = line & (npair - 1);
+    const int k = m <= half ? m : nx - m;
+    const CPair<T> v = ld_pair_stream(src + f * fstride + (long long)k * kstride + 2 * pr);
+    const C2<T> A = v.a, B = v.b;
+    if (k == 0 || k == half) return C2<T>{A.x, B.x};
+    if (m < half) return C2<T>{A.x - B.y, A.y + B.x};          // A + i B
+    return C2<T>{A.x + B.y, B.x - A.y};                         // conj(A) + i conj(B)
+  };
+  const FftPlan P = fft_plan<T>(lgx);
+  const int l0 = P.lgr(0);
+  fft_first_io_any<T, +1>(l0, lgx, NIN * npair, ld, sm);
+  return fft_lines_from<T, +1>(sm, sm2, lgx, NIN * npair, twx, 1);
 }
 
 // Forward-transform NOUT fields of packed row pairs (in `sm_in`, second buffer `sm2`) along x
