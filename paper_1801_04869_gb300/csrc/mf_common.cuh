@@ -46,25 +46,26 @@ template <typename T> __device__ __forceinline__ int dsm_off(const C2<T>* p) { r
 // Loads with L1 placement hints.  Tables (twiddles, wavenumbers) are read over and over and
 // should stay in L1 (evict_last); field data streams through once per pass and should not
 // displace them (no_allocate).  ldg_* use the read-only path and are only for data that no
-// thread writes during the launch; lds_* are coherent loads for data written by earlier phases.
+// thread writes during the launch (plain asm: the compiler may move and batch them); lds_* are
+// coherent loads for data written by earlier phases (volatile, ordered with the barriers).
 __device__ __forceinline__ C2<float> ldg_c2(const C2<float>* p) {
   float2 v;
-  asm volatile("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
   return {v.x, v.y};
 }
 __device__ __forceinline__ C2<double> ldg_c2(const C2<double>* p) {
   double2 v;
-  asm volatile("ld.global.nc.L1::evict_last.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  asm("ld.global.nc.L1::evict_last.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
   return {v.x, v.y};
 }
 __device__ __forceinline__ float ldg_tab(const float* p) {
   float v;
-  asm volatile("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ double ldg_tab(const double* p) {
   double v;
-  asm volatile("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ C2<float> lds_c2(const C2<float>* p) {
@@ -271,12 +272,24 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // Sum (or max) of partials[slot * max_items + i] over i < n, in a fixed order, computed
 // identically by every CTA.
+// The first warp does it alone (loads through L2 only: the partials were written by other CTAs
+// in this launch), so the CTA synchronises once instead of four times.
 __device__ __forceinline__ double reduce_partials(const double* partials, int max_items, int slot,
                                                   int n, bool is_max, double* red) {
-  const volatile double* p = partials + (size_t)slot * max_items;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) v = is_max ? fmax(v, p[i]) : v + p[i];
-  return is_max ? block_max(v, red) : block_sum(v, red);
+  const double* p = partials + (size_t)slot * max_items;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) {
+      const double x = __ldcg(p + i);
+      v = is_max ? fmax(v, x) : v + x;
+    }
+    v = is_max ? warp_max(v) : warp_sum(v);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double s = red[0];
+  __syncthreads();
+  return s;
 }
 
 // ------------------------------------------------------------------------------------------

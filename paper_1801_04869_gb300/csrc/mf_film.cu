@@ -92,13 +92,24 @@ struct Film {
       auto src = [=](int f, int l) { return Sin + f * nspec + (long long)(kx0 + l) * ny; };
       auto dst = [=](int g, int l) { return Sout + g * nspec + (long long)(kx0 + l) * ny; };
       const T s = (T)1 / (T)ncell;
+      // single precision: k_y = pi m / L_y (m in FFT order) and its Gaussian factor are
+      // computed from the index (a few ulp from the tables); double precision reads the tables
+      const T ky_scale = (T)(PI_D / d.Ly), g_half = (T)(0.5 * d.sigma * d.sigma);
       auto coef = [=](int l, int ky, T& kxo, T& kyo, T& k2, T& G) {
         const int kx = kx0 + l;
-        const T kxv = ldg_tab(&ktab[kx]), kyv = ldg_tab(&ktab[nkx + ky]);
+        const T kxv = ldg_tab(&ktab[kx]);
+        T kyv, gy;
+        if constexpr (sizeof(T) == 4) {
+          kyv = (T)(ky < ny / 2 ? ky : ky - ny) * ky_scale;
+          gy = __expf(-kyv * kyv * g_half);
+        } else {
+          kyv = ldg_tab(&ktab[nkx + ky]);
+          gy = ldg_tab(&gtab[nkx + ky]);
+        }
         kxo = (kx == half) ? (T)0 : kxv;
         kyo = (ky == ny / 2) ? (T)0 : kyv;
         k2 = kxv * kxv + kyv * kyv;
-        G = ldg_tab(&gtab[kx]) * ldg_tab(&gtab[nkx + ky]);
+        G = ldg_tab(&gtab[kx]) * gy;
       };
       if (op == OP_GRAD) {
         fft_round_trip<T, 1, 2>(sm, sm2, lgy, nl, twy, src, dst,
@@ -119,9 +130,18 @@ struct Film {
         fft_round_trip<T, 1, 1>(sm, sm2, lgy, nl, twy, src, dst,
             [=](int l, int ky, const C2<T>* x, C2<T>* y) {
               T kxo, kyo, k2, G; coef(l, ky, kxo, kyo, k2, G);
-              const T kabs = sqrt(k2);
+              // |k| and 1/|k| from one reciprocal square root in single precision (a few ulp,
+              // far below the FP32 transform error); correctly rounded sqrt and divide in double
+              T kabs, kinv;
+              if constexpr (sizeof(T) == 4) {
+                kinv = k2 > (T)0 ? rsqrtf(k2) : (T)0;
+                kabs = k2 * kinv;
+              } else {
+                kabs = sqrt(k2);
+                kinv = k2 > (T)0 ? (T)1 / kabs : (T)0;
+              }
               T m;
-              if (op == OP_K1) m = (k2 > (T)0) ? (T)2 / kabs : (T)0;
+              if (op == OP_K1) m = (T)2 * kinv;
               else if (op == OP_K2) m = lam * kabs * (T)0.5 * G;
               else if (op == OP_KH) m = kabs * (T)0.5;
               else m = (T)1;

@@ -158,14 +158,14 @@ __device__ __forceinline__ V4<double> ld4(const double* p) {
 // read-only for the whole launch (non-coherent path)
 __device__ __forceinline__ V4<float> ldg4(const float* p) {
   V4<float> r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "l"(p));
   return r;
 }
 __device__ __forceinline__ V4<double> ldg4(const double* p) {
   V4<double> r;
-  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p));
-  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[2]), "=d"(r.v[3]) : "l"(p + 2));
+  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(r.v[2]), "=d"(r.v[3]) : "l"(p + 2));
   return r;
 }
 __device__ __forceinline__ void st4(float* p, const V4<float>& v) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ void st4(double* p, const V4<double>& v) {
 }
 __device__ __forceinline__ uchar4 ldmask4(const uint8_t* p) {
   unsigned int w;
-  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(w) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(w) : "l"(p));
   return make_uchar4(w & 255u, (w >> 8) & 255u, (w >> 16) & 255u, w >> 24);
 }
 __device__ __forceinline__ int mask_at(const uchar4& m, int j) {
