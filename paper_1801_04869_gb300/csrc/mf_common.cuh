@@ -234,6 +234,29 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// sum over the CTA of single-precision partials (warp level in FP32, across warps in FP64);
+// result valid in all threads
+__device__ __forceinline__ double block_sum(float v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (l < NT / 32) ? red[l] : 0.0;
+    s = warp_sum(s);
+    if (l == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
 // sum over the CTA; result valid in all threads.  `red` holds NT/32 doubles of shared memory.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);

@@ -233,7 +233,7 @@ struct Film {
     // four consecutive cells of both rows of a pair per step; the epilogue issues its global
     // loads for the four cells together (x0 is a multiple of 4: one padding group)
     const int lgq = lgx - 2;
-#pragma unroll 2
+#pragma unroll 4
     for (int e = threadIdx.x; e < (npair << lgq); e += NT) {
       const int pr = e >> lgq, x0 = (e & ((1 << lgq) - 1)) << 2;
       V4<T> ina[NIN > 0 ? NIN : 1], inb[NIN > 0 ? NIN : 1], oa[NOUT > 0 ? NOUT : 1], ob[NOUT > 0 ? NOUT : 1];
