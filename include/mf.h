@@ -113,8 +113,10 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
 
 /* One right-hand side f(t, y) (Section 2.2 for films: Eqs. 9-12; Section 3.1 for bulk
    bodies: Eqs. 13-18).  d_y and d_ydot are device float64 state vectors.  The outside
-   iteration starts from the free-space solution of the previous call (warm start, Section
-   2.2) and updates it.  Returns MF_ERR_NOCONV when the iteration did not converge (d_ydot then
+   iteration starts from a previous free-space solution (Section 2.2): for films, that of the
+   last evaluation of the integrator's most recent accepted step (the previous time step) once
+   mf_advance/mf_step has accepted one, else that of the previous call; for bulk bodies, that
+   of the previous call.  Returns MF_ERR_NOCONV when the iteration did not converge (d_ydot then
    holds the last iterate).  *iters_out (may be NULL) receives the number of iterations. */
 mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, int* iters_out);
 
@@ -123,7 +125,8 @@ mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, in
 mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double* d_ydot,
                     int force_iters, int* iters_out);
 
-/* Forget the warm start: the next right-hand side starts from h_e_dot on free space. */
+/* Forget the warm starts (previous call and previous time step): the next right-hand side
+   starts from h_e_dot on free space. */
 mf_status mf_reset_warm(mf_problem* pb);
 
 /* Set the integrator state: time t, next step h (<= 0: default), state d_y (device, copied).

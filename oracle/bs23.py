@@ -21,8 +21,10 @@ Steps are clipped so that they end exactly on the next output time or h_e knot (
 10% of reaching it is stretched to it).  A step that ends on a knot discards k4 as the next k1,
 because h_e_dot jumps there; stage derivatives of h_e use the segment the step lies in.
 
-Every attempted step is logged; `replay` re-executes a logged sequence with the same step
-sizes, decisions and per-stage iteration counts (lock-step comparison with another solver).
+After an accepted step `on_accept()` is called (the film problem takes the last evaluation's
+free-space h_dot as the next initial approximation).  Every attempted step is logged; `replay`
+re-executes a logged sequence with the same step sizes, decisions and per-stage iteration
+counts (lock-step comparison with another solver).
 Pinned by tests/test_oracle_bs23.py: the stability polynomial 1+z+z^2/2+z^3/6 of one step on
 y' = lambda y, exactness on polynomial solutions (degree 3 for y_{n+1}, 2 for the embedded
 solution), third-order global convergence on y' = cos t, and the controller on a decaying ODE.
@@ -51,8 +53,9 @@ class LogEntry:
 class BS23:
     """Adaptive BS23 driver around a right-hand side rhs(t, y, seg, force_iters)."""
 
-    def __init__(self, rhs, waveform, *, rtol=1e-6, atol=1e-6, h0=0.0, h_min=1e-12):
+    def __init__(self, rhs, waveform, *, rtol=1e-6, atol=1e-6, h0=0.0, h_min=1e-12, on_accept=None):
         self.rhs = rhs
+        self.on_accept = on_accept            # called after every accepted step
         self.wf = waveform
         self.rtol, self.atol, self.h0, self.h_min = rtol, atol, h0, h_min
         self.log: list[LogEntry] = []
@@ -118,6 +121,8 @@ class BS23:
             outcome = forced.outcome
 
         if outcome == ACCEPT:
+            if self.on_accept is not None:
+                self.on_accept()
             self.t, self.y = t_new, ynew
             knot_hit = clipped and t_lim == self.wf.next_knot(t)
             self.k1 = None if knot_hit else k4

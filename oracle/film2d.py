@@ -20,8 +20,11 @@ Readings where the paper is silent (each also listed in the design doc):
   * odd multipliers (i k_x, i k_y) are zero at the Nyquist index; even ones keep it;
   * 2/|k| and the A, C constants are zero/absent at k = 0;
   * the returned g_dot is zeroed on free space (g stays exactly 0 there);
-  * the warm start is the converged free-space h_dot of the most recent call (first call: h_e_dot);
-    a call that fails with a residual above 1e3 tol (or not finite) leaves no warm start;
+  * the initial approximation is the free-space h_dot of the previous time step (Section 2.2):
+    the final iterate of the last call before the integrator's most recent accepted step
+    (`accept()`); before any accepted step, the iterate of the most recent call (first call:
+    h_e_dot); a call that fails with a residual above 1e3 tol (or not finite) leaves no
+    most-recent iterate;
   * the iteration stops without an update when it converges or reaches iter_max (then NOCONV);
   * iter_tol <= 0 runs exactly iter_max iterations and reports OK;
   * no free-space cells: a single pass with C = A = 0.
@@ -81,6 +84,7 @@ class FilmProblem:
         self.K2 = self.lam * (kabs / 2.0) * self.G                                  # Eq. 12
         self.Kh = kabs / 2.0                                                        # h_z readout
         self.warm = None          # free-space h_dot of the most recent call
+        self.committed = None     # free-space h_dot of the previous (accepted) time step
         self.last = {}
 
     # ---- spectral operators --------------------------------------------------------------
@@ -128,8 +132,14 @@ class FilmProblem:
             self.last = dict(C=0.0, A=0.0, r=0.0)
             return u, 1, OK
 
-        # initial approximation and the shift A^0 of Eq. 10
-        warm = self.warm if self.warm is not None else np.full((self.ny, self.nx), he_dot)
+        # initial approximation (the previous time step's h_dot, Section 2.2) and the shift A^0
+        # of Eq. 10
+        if self.committed is not None:
+            warm = self.committed
+        elif self.warm is not None:
+            warm = self.warm
+        else:
+            warm = np.full((self.ny, self.nx), he_dot)
         hd = np.where(self.out, warm, h_in)
         A = (hd.sum() - N * he_dot) / n_out
         hd = np.where(self.out, hd - A, hd)
@@ -159,6 +169,16 @@ class FilmProblem:
             self.warm = None       # a diverged iterate is no warm start; the next call starts cold
         self.last = dict(C=C, A=A, r=r, hdot=hd)
         return np.where(self.conductor, gd, 0.0), i + 1, status
+
+    def accept(self) -> None:
+        """The integrator accepted a step whose last evaluation was the most recent call: its
+        free-space h_dot becomes the initial approximation of later calls."""
+        if self.warm is not None:
+            self.committed = self.warm.copy()
+
+    def reset_warm(self) -> None:
+        self.warm = None
+        self.committed = None
 
     # ---- readouts ------------------------------------------------------------------------
     def hz(self, t: float, g: np.ndarray) -> np.ndarray:

@@ -35,7 +35,7 @@ int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t Sa, Sb, hd, u, q1, q2, jc, mask, twx, twy, twz, ktab, gtab, fbuf[6], partials, st, gb,
+  size_t Sa, Sb, hd, hd2, u, q1, q2, jc, mask, twx, twy, twz, ktab, gtab, fbuf[6], partials, st, gb,
       log, knots, mscr, desc, total;
   long long ncell, nspec, nstate;
   int max_items;
@@ -79,6 +79,7 @@ Layout layout(const mf_params* p) {
   L.Sa = take(3 * L.nspec * 2 * ts);
   L.Sb = take(3 * L.nspec * 2 * ts);
   L.hd = take(ncomp * L.ncell * ts);
+  L.hd2 = take(p->dim == 2 ? L.ncell * ts : 0);
   L.u = take(p->dim == 2 ? L.ncell * ts : 0);
   L.q1 = take(p->dim == 2 ? L.ncell * ts : 0);
   L.q2 = take(p->dim == 2 ? L.ncell * ts : 0);
@@ -234,7 +235,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
     if (p->mask[i] > 2) { delete pb; return MF_ERR_ARG; }
   d.nout = nout;
   char* w = pb->ws;
-  d.Sa = w + L.Sa; d.Sb = w + L.Sb; d.hd = w + L.hd; d.u = w + L.u; d.q1 = w + L.q1; d.q2 = w + L.q2;
+  d.Sa = w + L.Sa; d.Sb = w + L.Sb; d.hd = w + L.hd; d.hd2 = p->dim == 2 ? (void*)(w + L.hd2) : d.hd; d.u = w + L.u; d.q1 = w + L.q1; d.q2 = w + L.q2;
   d.jcmap = p->jc_map ? (const void*)(w + L.jc) : nullptr;
   d.mask = (const uint8_t*)(w + L.mask);
   d.tw_x = w + L.twx; d.tw_y = w + L.twy; d.tw_z = w + L.twz;
@@ -374,6 +375,9 @@ mf_status mf_reset_warm(mf_problem* pb) {
   if (r != MF_OK) return r;
   s.warm_valid = 0;
   s.A_prev = 0.0;
+  s.com_valid = 0;
+  s.hd_sel = 0;
+  s.A_com = 0.0;
   return write_state(pb, &s);
 }
 

@@ -501,6 +501,7 @@ struct BulkRhs {
                                const double* k3, const double* y, const double* yn) {
     return bulk_rhs<T>(B, t, seg, in, kout, force, want_err, h, k1, k2, k3, y, yn);
   }
+  __device__ void on_accept() {}     // 3D: every call starts from the most recent iterate
 };
 
 template <typename T>

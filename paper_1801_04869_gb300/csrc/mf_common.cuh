@@ -98,7 +98,10 @@ struct StepLog {                 // one attempted BS23 step
 struct SolverState {
   double t, h;
   double A_prev;                 // shift still to subtract on free space from the warm h_dot (2D)
-  int warm_valid;                // 0: the next call starts from h_e_dot
+  int warm_valid;                // the most recent call's h_dot iterate is a usable start
+  int com_valid;                 // (2D) an accepted step's h_dot is the initial approximation
+  int hd_sel;                    // (2D) h_dot buffer the next call writes; the other one is committed
+  double A_com;                  // (2D) shift still to subtract from the committed h_dot
   int k1_valid;                  // first-same-as-last derivative available
   int failed;                    // the previous attempt was rejected
   int ybuf, ynewbuf, k1buf, k4buf;   // rotation of the FP64 state buffers
@@ -108,7 +111,7 @@ struct SolverState {
   long long log_count;
   double last_r;                 // last convergence residual
   double last_err;
-  double pad[4];
+  double pad[3];
 };
 
 // Barrier state of one launch (zeroed before every launch).  `count` is a monotonic arrival
@@ -147,6 +150,7 @@ struct Desc {
   void* Sa;                      // spectra, 3 fields
   void* Sb;                      // spectra, 3 fields (3D: second buffer of the transpose chain)
   void* hd;                      // h_dot iterate (1 or 3 fields)
+  void* hd2;                     // second h_dot buffer (2D: the previous time step's h_dot)
   void* u;                       // raw g_dot (2D)
   void* q1;                      // F^-1[K1 F(out)] (2D)
   void* q2;                      // F^-1[K2 F(out)] (2D)

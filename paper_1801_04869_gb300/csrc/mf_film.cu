@@ -361,11 +361,12 @@ template <typename T>
 struct EpiInit : EpiBase<T, T> {
   FilmPtrs<T> P;
   bool warm;
+  const T* wsrc;          // warm start (the previous time step's or the most recent iterate)
   T A_prev, hed;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     V4<T> w;
-    if (warm) w = ld4(P.hd + i);
+    if (warm) w = ld4(wsrc + i);
     V4<T> h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -493,6 +494,9 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   const double hed = he_dot(d, t, seg);
   const double N = (double)F.ncell;
   const double nout = (double)d.nout;
+  // h_dot buffers: this call writes hdw; hdc holds the committed (accepted-step) h_dot
+  T* const hdw = (T*)(F.sh.hd_sel ? d.hd2 : d.hd);
+  const T* const hdc = (const T*)(F.sh.hd_sel ? d.hd : d.hd2);
 
   // P1
   {
@@ -513,8 +517,13 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   const bool have_out = d.nout > 0;
   {
-    EpiInit<T> e; e.P = F.ptrs();
-    e.warm = F.sh.warm_valid != 0; e.A_prev = (T)F.sh.A_prev; e.hed = (T)hed;
+    // initial approximation: the previous time step's h_dot when the integrator has accepted a
+    // step (Section 2.2), else the most recent call's iterate, else h_e_dot
+    EpiInit<T> e; e.P = F.ptrs(); e.P.hd = hdw;
+    const bool com = F.sh.com_valid != 0;
+    e.warm = com || F.sh.warm_valid != 0;
+    e.wsrc = com ? hdc : hdw;
+    e.A_prev = (T)(com ? F.sh.A_com : F.sh.A_prev); e.hed = (T)hed;
     F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                              // P5
   }
   if (!F.sync(5)) { res.status = ST_BARRIER; return res; }
@@ -560,7 +569,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     const bool stop = (forced || fixed) ? last : (r < d.iter_tol || last);
     if (stop) break;
     {
-      EpiUpdate<T> e; e.P = F.ptrs(); e.A = (T)A; e.C = (T)C;
+      EpiUpdate<T> e; e.P = F.ptrs(); e.P.hd = hdw; e.A = (T)A; e.C = (T)C;
       F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                            // P10
     }
     if (!F.sync(10)) { res.status = ST_BARRIER; return res; }
@@ -598,6 +607,16 @@ struct FilmRhs {
                                const double* k3, const double* y, const double* yn) {
     return film_rhs<T>(F, t, seg, in, kout, force, want_err, h, k1, k2, k3, y, yn);
   }
+  // the integrator accepted a step: the last call's h_dot (written to hd_sel) becomes the
+  // committed initial approximation, and later calls write the other buffer
+  __device__ void on_accept() {
+    __syncthreads();
+    const int sel = F.sh.hd_sel;
+    const double A = F.sh.A_prev;
+    __syncthreads();
+    if (threadIdx.x == 0) { F.sh.com_valid = 1; F.sh.A_com = A; F.sh.hd_sel = sel ^ 1; }
+    __syncthreads();
+  }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -616,6 +635,9 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(const Desc* __restrict__ dg
     sh.warm_valid = st->warm_valid;
     sh.bar_passed = 0;
     sh.A_prev = st->A_prev;
+    sh.com_valid = st->com_valid;
+    sh.hd_sel = st->hd_sel;
+    sh.A_com = st->A_com;
   }
   if (threadIdx.x == 0) new (objraw) Film<T>(d, sm, sh);
   __syncthreads();
@@ -665,6 +687,9 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(const Desc* __restrict__ dg
   if (leader) {
     st->warm_valid = sh.warm_valid;
     st->A_prev = sh.A_prev;
+    st->com_valid = sh.com_valid;
+    st->hd_sel = sh.hd_sel;
+    st->A_com = sh.A_com;
     st->status = status;
   }
 }

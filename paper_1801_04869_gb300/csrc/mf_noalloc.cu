@@ -123,7 +123,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
     nout += p->mask[i] == 0;
   }
   d.nout = nout;
-  d.Sa = w + oSa; d.Sb = w + oSb; d.hd = w + ohd; d.u = w + ou; d.q1 = w + oq1; d.q2 = w + oq2;
+  d.Sa = w + oSa; d.Sb = w + oSb; d.hd = w + ohd; d.hd2 = d.hd; d.u = w + ou; d.q1 = w + oq1; d.q2 = w + oq2;
   d.jcmap = p->jc_map ? (const void*)(w + ojc) : nullptr;
   d.mask = (const uint8_t*)(w + omask);
   d.tw_x = w + otwx; d.tw_y = w + otwy; d.tw_z = w + otwz;

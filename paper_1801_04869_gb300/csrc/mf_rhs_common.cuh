@@ -24,6 +24,8 @@ struct Shared {
   double A, C, r, hed;
   int warm_valid;
   double A_prev;
+  int com_valid, hd_sel;         // (2D) accepted-step initial approximation, see SolverState
+  double A_com;
   unsigned long long bar_passed;  // grid barriers passed in this launch (thread 0)
 };
 
@@ -156,6 +158,7 @@ __device__ int bs23_advance(Rhs& R, const Desc& d, SolverState* st, const Kernel
       if (leader) st->log_count += 1;
       ++att;
       if (outcome == 1) {
+        R.on_accept();                 // the last evaluation's iterate starts later calls
         const bool knot_hit = clipped && t_lim == he_next_knot(d, t);
         t = t_new;
         int tmp = iy; iy = iyn; iyn = tmp;
