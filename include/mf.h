@@ -141,6 +141,16 @@ mf_status mf_get_state(mf_problem* pb, double* t, double* h, double* d_y);
    clipped to end on t_target and on h_e knots. */
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts);
 
+/* Advance n independent problems (films or bulk bodies) to t_targets[i] (as mf_advance), at
+   the same time: the persistent kernel of every problem is launched on that problem's stream
+   before any is waited for, so problems whose launch grids leave room on the GPU (small films)
+   run concurrently.  Give each problem its own stream at mf_create for that.  Batching has no
+   counterpart in the paper: it is how many independent magnetization problems (a parameter or
+   geometry sweep) share one GPU.  statuses (may be NULL) receives each problem's status; the
+   return value is the first non-OK one (MF_OK if all succeeded).  pbs must not repeat a problem. */
+mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_targets,
+                           long long max_attempts, mf_status* statuses);
+
 /* One BS23 step attempt towards t_max; *accepted (may be NULL) is 1 if it was accepted. */
 mf_status mf_step(mf_problem* pb, double t_max, int* accepted);
 

@@ -155,12 +155,17 @@ mf_status write_state(mf_problem* pb, const SolverState* s) {
   return MF_OK;
 }
 
-mf_status launch(mf_problem* pb, const KernelArgs& a) {
+// enqueue one persistent launch on the problem's stream (no wait)
+mf_status launch_enqueue(mf_problem* pb, const KernelArgs& a) {
   MF_CUDA(pb, cudaSetDevice(pb->device));
   MF_CUDA(pb, cudaMemsetAsync(pb->d.gb, 0, sizeof(GridBarrier), pb->stream));
   cudaError_t e = pb->d.dim == 2 ? film_launch(pb->d.precision, pb->d, a, pb->stream)
                                  : bulk_launch(pb->d.precision, pb->d, a, pb->stream);
   if (e != cudaSuccess) return cuda_fail(pb, e, "persistent kernel launch");
+  return MF_OK;
+}
+// wait for the problem's stream and turn the kernel's sticky status into the return value
+mf_status launch_finish(mf_problem* pb) {
   SolverState s;
   mf_status r = read_state(pb, &s);
   if (r != MF_OK) return r;
@@ -172,6 +177,11 @@ mf_status launch(mf_problem* pb, const KernelArgs& a) {
     return (mf_status)s.status;
   }
   return MF_OK;
+}
+
+mf_status launch(mf_problem* pb, const KernelArgs& a) {
+  mf_status r = launch_enqueue(pb, a);
+  return r != MF_OK ? r : launch_finish(pb);
 }
 
 }  // namespace
@@ -431,6 +441,29 @@ mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {
   KernelArgs a{};
   a.mode = MODE_ADVANCE; a.t_target = t_target; a.max_attempts = max_attempts;
   return launch(pb, a);
+}
+
+mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_targets,
+                           long long max_attempts, mf_status* statuses) {
+  if (!pbs || !t_targets || n < 0) return MF_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!pbs[i]) return MF_ERR_ARG;
+  std::vector<mf_status> st(n, MF_OK);
+  for (int i = 0; i < n; ++i) st[i] = ensure_h(pbs[i], t_targets[i]);
+  // all launches first, each on its problem's stream, then the waits
+  for (int i = 0; i < n; ++i) {
+    if (st[i] != MF_OK) continue;
+    KernelArgs a{};
+    a.mode = MODE_ADVANCE; a.t_target = t_targets[i]; a.max_attempts = max_attempts;
+    st[i] = launch_enqueue(pbs[i], a);
+  }
+  mf_status first = MF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st[i] == MF_OK) st[i] = launch_finish(pbs[i]);
+    if (statuses) statuses[i] = st[i];
+    if (first == MF_OK) first = st[i];
+  }
+  return first;
 }
 
 mf_status mf_step(mf_problem* pb, double t_max, int* accepted) {

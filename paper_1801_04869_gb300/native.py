@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_NOCONV
 EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf_rhs_ex",
            "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
-           "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc"]
+           "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch"]
 
 
 class mf_params(ctypes.Structure):
@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
         "mf_set_state": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, vp]),
         "mf_get_state": (ctypes.c_int, [vp, dp, dp, vp]),
         "mf_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_longlong]),
+        "mf_advance_batch": (ctypes.c_int, [P(vp), ctypes.c_int, dp, ctypes.c_longlong, ip]),
         "mf_step": (ctypes.c_int, [vp, ctypes.c_double, ip]),
         "mf_run_ramp": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, vp]),
         "mf_readout": (ctypes.c_int, [vp, ctypes.c_int, vp]),
@@ -277,6 +278,23 @@ def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int 
                                  force_iters, ctypes.c_void_p(s.cuda_stream), ctypes.byref(it),
                                  msg, 256)
     return st, it.value, msg.value.decode()
+
+
+def advance_batch(problems, t_targets, max_attempts: int = 1 << 40):
+    """mf_advance_batch: advance several problems together, each launched on its own stream
+    before any is waited for.  Returns the list of per-problem status codes; raises on the first
+    failure like the single-problem calls."""
+    lib = load()
+    n = len(problems)
+    hs = (ctypes.c_void_p * n)(*[p.h for p in problems])
+    ts = (ctypes.c_double * n)(*[float(t) for t in t_targets])
+    st = (ctypes.c_int * n)()
+    r = lib.mf_advance_batch(hs, n, ts, max_attempts, st)
+    out = list(st)
+    if r != 0:
+        bad = next(i for i, v in enumerate(out) if v != 0)
+        raise MFError(r, f"problem {bad}: " + lib.mf_last_error(problems[bad].h).decode())
+    return out
 
 
 def from_workload(wl, **over) -> Problem:

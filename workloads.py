@@ -211,3 +211,32 @@ def cube_bulk(n_grid: int = 128, precision: int = 1) -> Workload:
                     n=25.0, rho_out=5.0, precision=precision, t0=0.0, t1=1.0,
                     he_knots=((0.0, 0.5, 1.0), (0.0, 0.25, 0.25)), iter_tol=1e-4)
 
+
+
+def film_batch(count: int = 256, seed: int = 3, max_side: int = 512, precision: int = 1) -> list[Workload]:
+    """Independent films of a parameter/geometry sweep: the shape class is uniform over
+    {square, rectangle with aspect U[1, 2], disk}, the film side s (cells) over 64 .. max_side,
+    the power n over {19, 30, 50} and the ramp amplitude (h_e from 0 to it over [0, 1]) over
+    U[0.2, 1].  The film's long side spans [-1, 1] with s cells; the periodic grid is the next
+    power of two >= 2 s cells per axis (at least twice the film, as the paper's examples),
+    D = [-L, L]^2 with L = grid / s.""" 
+    r = rng(seed)
+    out = []
+    for i in range(count):
+        cls = int(r.integers(0, 3))
+        s = int(r.integers(64, max_side + 1))
+        n = float((19.0, 30.0, 50.0)[int(r.integers(0, 3))])
+        amp = float(r.uniform(0.2, 1.0))
+        aspect = float(r.uniform(1.0, 2.0))
+        grid = 1 << int(np.ceil(np.log2(2 * s)))
+        L = 2.0 * grid / (2 * s)            # film long half-side 1 with s cells across it
+        if cls == 0:
+            m, name = film_mask(grid, grid, L, L, "rect", ax=1.0, ay=1.0), "square"
+        elif cls == 1:
+            m, name = film_mask(grid, grid, L, L, "rect", ax=1.0, ay=1.0 / aspect), "rect"
+        else:
+            m, name = film_mask(grid, grid, L, L, "disk", radius=1.0), "disk"
+        out.append(Workload(f"batch{seed}_{i}_{name}_{s}_in_{grid}", 2, grid, grid, 1, L, L, 0.0, m,
+                            n=n, rho_out=1.0, precision=precision, t0=0.0, t1=1.0,
+                            he_knots=((0.0, 1.0), (0.0, amp)), rtol=1e-3, atol=1e-6))
+    return out
