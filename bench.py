@@ -225,7 +225,7 @@ def full_ramp_leg(native, W, torch, precision: int):
     sec = time.perf_counter() - w0
     info = p.mf_get_info()
     o = _oracle_problem(wl)
-    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept)
+    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept, on_attempt=o.begin_attempt)
     s.start(0.0, np.zeros((wl.ny, wl.nx)), 1.0)
     c0 = time.perf_counter()
     s.advance(1.0)

@@ -21,8 +21,8 @@ Steps are clipped so that they end exactly on the next output time or h_e knot (
 10% of reaching it is stretched to it).  A step that ends on a knot discards k4 as the next k1,
 because h_e_dot jumps there; stage derivatives of h_e use the segment the step lies in.
 
-After an accepted step `on_accept()` is called (the film problem takes the last evaluation's
-free-space h_dot as the next initial approximation).  Every attempted step is logged; `replay`
+Before every attempt `on_attempt()` and after an accepted step `on_accept()` are called (the
+film problem starts an attempt from the accepted step's free-space h_dot).  Every attempted step is logged; `replay`
 re-executes a logged sequence with the same step sizes, decisions and per-stage iteration
 counts (lock-step comparison with another solver).
 Pinned by tests/test_oracle_bs23.py: the stability polynomial 1+z+z^2/2+z^3/6 of one step on
@@ -53,9 +53,11 @@ class LogEntry:
 class BS23:
     """Adaptive BS23 driver around a right-hand side rhs(t, y, seg, force_iters)."""
 
-    def __init__(self, rhs, waveform, *, rtol=1e-6, atol=1e-6, h0=0.0, h_min=1e-12, on_accept=None):
+    def __init__(self, rhs, waveform, *, rtol=1e-6, atol=1e-6, h0=0.0, h_min=1e-12, on_accept=None,
+                 on_attempt=None):
         self.rhs = rhs
         self.on_accept = on_accept            # called after every accepted step
+        self.on_attempt = on_attempt          # called before the first evaluation of every attempt
         self.wf = waveform
         self.rtol, self.atol, self.h0, self.h_min = rtol, atol, h0, h_min
         self.log: list[LogEntry] = []
@@ -79,6 +81,8 @@ class BS23:
 
     def attempt(self, t_target: float, forced: LogEntry | None = None) -> int:
         """One step attempt towards t_target.  Returns its outcome."""
+        if self.on_attempt is not None:
+            self.on_attempt()
         t, y = self.t, self.y
         t_lim = min(t_target, self.wf.next_knot(t))
         if forced is None:

@@ -20,11 +20,12 @@ Readings where the paper is silent (each also listed in the design doc):
   * odd multipliers (i k_x, i k_y) are zero at the Nyquist index; even ones keep it;
   * 2/|k| and the A, C constants are zero/absent at k = 0;
   * the returned g_dot is zeroed on free space (g stays exactly 0 there);
-  * the initial approximation is the free-space h_dot of the previous time step (Section 2.2):
-    the final iterate of the last call before the integrator's most recent accepted step
-    (`accept()`); before any accepted step, the iterate of the most recent call (first call:
-    h_e_dot); a call that fails with a residual above 1e3 tol (or not finite) leaves no
-    most-recent iterate;
+  * the initial approximation is the free-space h_dot "from the previous time step" (Section
+    2.2): the first evaluation of a step attempt (`begin_attempt()`) starts from the final
+    iterate of the last evaluation of the integrator's most recent accepted step (`accept()`);
+    the later stages of the attempt, and calls outside the integrator, start from the iterate
+    of the most recent call (first call: h_e_dot); a call that fails with a residual above
+    1e3 tol (or not finite) leaves no most-recent iterate;
   * the iteration stops without an update when it converges or reaches iter_max (then NOCONV);
   * iter_tol <= 0 runs exactly iter_max iterations and reports OK;
   * no free-space cells: a single pass with C = A = 0.
@@ -85,6 +86,7 @@ class FilmProblem:
         self.Kh = kabs / 2.0                                                        # h_z readout
         self.warm = None          # free-space h_dot of the most recent call
         self.committed = None     # free-space h_dot of the previous (accepted) time step
+        self.attempt_first = False    # the next call is the first of a step attempt
         self.last = {}
 
     # ---- spectral operators --------------------------------------------------------------
@@ -134,7 +136,8 @@ class FilmProblem:
 
         # initial approximation (the previous time step's h_dot, Section 2.2) and the shift A^0
         # of Eq. 10
-        if self.committed is not None:
+        first, self.attempt_first = self.attempt_first, False
+        if first and self.committed is not None:
             warm = self.committed
         elif self.warm is not None:
             warm = self.warm
@@ -176,9 +179,14 @@ class FilmProblem:
         if self.warm is not None:
             self.committed = self.warm.copy()
 
+    def begin_attempt(self) -> None:
+        """The integrator starts a step attempt: its first call starts from the accepted step."""
+        self.attempt_first = True
+
     def reset_warm(self) -> None:
         self.warm = None
         self.committed = None
+        self.attempt_first = False
 
     # ---- readouts ------------------------------------------------------------------------
     def hz(self, t: float, g: np.ndarray) -> np.ndarray:

@@ -502,6 +502,7 @@ struct BulkRhs {
     return bulk_rhs<T>(B, t, seg, in, kout, force, want_err, h, k1, k2, k3, y, yn);
   }
   __device__ void on_accept() {}     // 3D: every call starts from the most recent iterate
+  __device__ void on_attempt() {}
 };
 
 template <typename T>

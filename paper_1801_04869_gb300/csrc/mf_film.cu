@@ -494,6 +494,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   const double hed = he_dot(d, t, seg);
   const double N = (double)F.ncell;
   const double nout = (double)d.nout;
+  const bool first = F.sh.attempt_first != 0;   // read by every thread before it is cleared
   // h_dot buffers: this call writes hdw; hdc holds the committed (accepted-step) h_dot
   T* const hdw = (T*)(F.sh.hd_sel ? d.hd2 : d.hd);
   const T* const hdc = (const T*)(F.sh.hd_sel ? d.hd : d.hd2);
@@ -517,10 +518,11 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   const bool have_out = d.nout > 0;
   {
-    // initial approximation: the previous time step's h_dot when the integrator has accepted a
-    // step (Section 2.2), else the most recent call's iterate, else h_e_dot
+    // initial approximation "from the previous time step" (Section 2.2): the first evaluation
+    // of a step attempt starts from the accepted step's h_dot, later stages (and calls outside
+    // the integrator) from the most recent call's iterate; the very first call from h_e_dot
     EpiInit<T> e; e.P = F.ptrs(); e.P.hd = hdw;
-    const bool com = F.sh.com_valid != 0;
+    const bool com = first && F.sh.com_valid != 0;
     e.warm = com || F.sh.warm_valid != 0;
     e.wsrc = com ? hdc : hdw;
     e.A_prev = (T)(com ? F.sh.A_com : F.sh.A_prev); e.hed = (T)hed;
@@ -583,6 +585,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   const bool diverged = res.status == ST_NOCONV && !(r < 1e3 * d.iter_tol);
   F.sh.warm_valid = diverged ? 0 : 1;
   F.sh.A_prev = A;
+  F.sh.attempt_first = 0;
 
   // finalize
   {
@@ -609,6 +612,11 @@ struct FilmRhs {
   }
   // the integrator accepted a step: the last call's h_dot (written to hd_sel) becomes the
   // committed initial approximation, and later calls write the other buffer
+  __device__ void on_attempt() {
+    __syncthreads();
+    if (threadIdx.x == 0) F.sh.attempt_first = 1;
+    __syncthreads();
+  }
   __device__ void on_accept() {
     __syncthreads();
     const int sel = F.sh.hd_sel;
@@ -638,6 +646,7 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(const Desc* __restrict__ dg
     sh.com_valid = st->com_valid;
     sh.hd_sel = st->hd_sel;
     sh.A_com = st->A_com;
+    sh.attempt_first = 0;
   }
   if (threadIdx.x == 0) new (objraw) Film<T>(d, sm, sh);
   __syncthreads();

@@ -26,6 +26,7 @@ struct Shared {
   double A_prev;
   int com_valid, hd_sel;         // (2D) accepted-step initial approximation, see SolverState
   double A_com;
+  int attempt_first;             // (2D) the next right-hand side is the first of a step attempt
   unsigned long long bar_passed;  // grid barriers passed in this launch (thread 0)
 };
 
@@ -104,6 +105,7 @@ __device__ int bs23_advance(Rhs& R, const Desc& d, SolverState* st, const Kernel
       const double t_lim = fmin(a.t_target, he_next_knot(d, t));
       const bool clipped = t + 1.1 * h >= t_lim;
       if (clipped) h = t_lim - t;
+      R.on_attempt();                  // the attempt's first evaluation starts from the accepted step
       const int seg = he_segment(d, t);
       int it[4] = {-1, -1, -1, -1};
       double* y = d.fbuf[iy];

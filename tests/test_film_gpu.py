@@ -131,7 +131,7 @@ def test_rhs_full_size_rect_film_2048_fp32():
 
 
 def _replay(o, wl, log, y0):
-    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept)
+    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept, on_attempt=o.begin_attempt)
     s.start(wl.t0, y0, wl.t1)
     entries = [LogEntry(t, h, tn, oc, it, err) for (t, h, tn, oc, it, err) in log]
     s.replay(entries)
@@ -169,7 +169,7 @@ def test_ramp_fp32_free_running_config1():
     t_out = np.array([0.25, 0.5, 0.75, 1.0])
     m, hz = p.mf_run_ramp(t_out, want_fields=True)
     o = oracle_of(wl)
-    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept)
+    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept, on_attempt=o.begin_attempt)
     s.start(0.0, np.zeros((128, 128)), 1.0)
     for k, t in enumerate(t_out):
         s.advance(t)

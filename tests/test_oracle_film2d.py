@@ -161,7 +161,7 @@ def test_bean_strip_critical_state():
     wf = Waveform((0.0, 1.0), (0.0, he_end))
     p = FilmProblem(nx, ny, Lx, Ly, mask, n=50.0, rho_out=1.0, waveform=wf,
                     iter_tol=2e-4, iter_max=20000)
-    s = BS23(p.rhs, wf, rtol=1e-5, atol=1e-5, on_accept=p.accept)
+    s = BS23(p.rhs, wf, rtol=1e-5, atol=1e-5, on_accept=p.accept, on_attempt=p.begin_attempt)
     s.start(0.0, np.zeros((ny, nx)), 1.0)
     assert s.advance(1.0) == OK
     j = p.sheet_current(s.y)[0][:, 0]
