@@ -82,7 +82,7 @@ struct Bulk {
 
   // ---- x pass over rows (z, y0 .. y0 + rb): inverse of NIN = 0|3 fields, epilogue, forward ----
   template <int NIN, int NOUT, class Epi>
-  __device__ __noinline__ void xitem(int z, int y0, Epi& epi_io) {
+  __device__ __forceinline__ void xitem(int z, int y0, Epi& epi_io) {
     Epi epi = epi_io;                   // register copy of the epilogue
     const int nx = this->nx, ny = this->ny, lgx = this->lgx, nkx = this->nkx, rb = this->rb;
     const long long nspec = this->nspec;

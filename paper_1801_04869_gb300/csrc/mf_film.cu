@@ -215,8 +215,9 @@ struct Film {
   // ---- x pass over rows [y0, y0 + rb): inverse of NIN fields, epilogue, forward of NOUT ----
   // epi(row, x, in[], out[]) is called for every cell of the item.
   template <int NIN, int NOUT, class Epi>
-  __device__ __noinline__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi_io) {
-    // work on register copies: the epilogue and the members used in the loops
+  __device__ __forceinline__ void row_item(int y0, int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi_io) {
+    // inlined into the pass loop (a call per item cost a save and restore of the caller's live
+    // registers); works on register copies of the epilogue and of the members used in the loops
     Epi epi = epi_io;
     C2<T>* const smA = sm;
     C2<T>* const smB = sm2;
