@@ -177,3 +177,38 @@ def test_bean_strip_critical_state():
     assert np.all(np.sign(j[pen]) == np.sign(y[pen]))                  # shielding sense
     assert np.abs(hz[core]).max() < 0.01 * he_end
     assert hz[pen].min() > 0.3 * he_end
+
+
+def test_attempts_start_from_the_accepted_step():
+    """Reading of 'the previous time step' (Section 2.2): after an accepted step the first
+    evaluation of the next attempt starts from that step's final free-space h_dot, whatever the
+    most recent call left; the later stages of an attempt start from the preceding stage."""
+    n, L = 32, 2.0
+    mask = W.film_mask(n, n, L, L, "rect", ax=1.0, ay=1.0)
+    wf = Waveform((0.0, 1.0), (0.0, 0.5))
+    kw = dict(n=19.0, rho_out=1.0, waveform=wf, iter_tol=2e-4, iter_max=3000)
+    p = FilmProblem(n, n, L, L, mask, **kw)
+    s = BS23(p.rhs, wf, rtol=1e-6, atol=1e-6, on_accept=p.accept, on_attempt=p.begin_attempt)
+    g0 = W.film_state(mask, L, L, seed=21, amplitude=0.3)
+    s.start(0.0, g0, 1.0)
+    while s.attempt(1.0) != 1:
+        pass
+    # the accepted step's last evaluation (k4) left its iterate as the committed start
+    assert p.committed is not None and np.array_equal(p.committed, p.warm)
+    committed = p.committed.copy()
+    # a stage outside an attempt start ignores the committed field ...
+    p.warm = np.full_like(p.warm, 0.37)
+    q = FilmProblem(n, n, L, L, mask, **kw)
+    q.warm = p.warm.copy()
+    a, _, _ = p.rhs(s.t, s.y, None, 3)
+    b, _, _ = q.rhs(s.t, s.y, None, 3)
+    assert np.array_equal(a, b)
+    # ... while the first evaluation of an attempt starts from it
+    p.warm = np.full_like(p.warm, 0.37)
+    p.begin_attempt()
+    a, _, _ = p.rhs(s.t, s.y, None, 3)
+    q = FilmProblem(n, n, L, L, mask, **kw)
+    q.warm = committed
+    b, _, _ = q.rhs(s.t, s.y, None, 3)
+    assert np.array_equal(a, b)
+    assert p.attempt_first is False
