@@ -51,7 +51,7 @@ class LogEntry:
 
 
 class BS23:
-    """Adaptive BS23 driver around a right-hand side rhs(t, y, seg, force_iters)."""
+    """Adaptive BS23 integrator around a right-hand side rhs(t, y, seg, force_iters)."""
 
     def __init__(self, rhs, waveform, *, rtol=1e-6, atol=1e-6, h0=0.0, h_min=1e-12, on_accept=None,
                  on_attempt=None):

@@ -11,7 +11,7 @@ Follows Section 3.1 of Prigozhin & Sokolovsky in float64 and in the paper's orde
   all derivatives are Gaussian-smoothed spectral derivatives, sigma = sqrt(dx^2+dy^2+dz^2)
   (Section 3.1, last paragraph; Section 3.2).
 
-Readings where the paper is silent (also in the design doc):
+Readings where the paper is silent:
   * odd multipliers i k_c are zero at the Nyquist index of axis c, in the curls and in Phi;
     Phi carries no Gaussian;
   * the conductor (mask 1 superconductor, mask 2 normal cutting layer) keeps h_dot_in and

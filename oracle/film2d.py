@@ -15,7 +15,7 @@ problems in type-II superconductivity, in float64 and in the paper's order:
   stop    mean over free space of |g_dot^i| < tol = 2e-4 (Section 2.3), tested before the update
   h_z     h_z = h_e + F^-1[(|k|/2) F g]  (end of Section 2.1)
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * cell-centred grid x_i = -L + (i+1/2) dx; k = pi m / L with m in FFT order;
   * odd multipliers (i k_x, i k_y) are zero at the Nyquist index; even ones keep it;
   * 2/|k| and the A, C constants are zero/absent at k = 0;

@@ -602,7 +602,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   return res;
 }
 
-// adapter used by the shared BS23 driver
+// adapter used by the shared BS23 integrator loop
 template <typename T>
 struct FilmRhs {
   Film<T>& F;

@@ -82,7 +82,7 @@ struct RhsOut {
 
 
 // ------------------------------------------------------------------------------------------
-// BS23 driver shared by the film and bulk kernels: adaptive steps until t_target or
+// BS23 integrator loop shared by the film and bulk kernels: adaptive steps until t_target or
 // max_attempts, first same as last, every decision taken identically by every CTA.
 // R(t, seg, stage_in, k_out, force_iters, want_err, h, k1, k2, k3, y, ynew) evaluates one
 // right-hand side.  Returns the launch status.
