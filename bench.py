@@ -241,6 +241,20 @@ def full_ramp_leg(native, W, torch, precision: int):
             "oracle_seconds": cpu_sec}
 
 
+def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's timed seconds, the evaluations of
+    all ranks and the sum of the ranks' end-to-end rates (the replicas run side by side).
+    `dist` is torch.distributed with an initialised process group, or None for one rank."""
+    if dist is None:
+        return sec, float(n_rhs), e2e_rate
+    import torch
+    mx = torch.tensor([sec], device=device, dtype=torch.float64)
+    sm = torch.tensor([float(n_rhs), e2e_rate], device=device, dtype=torch.float64)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0]), float(sm[1])
+
+
 def cores_used() -> int:
     # numpy's FFT (pocketfft) and elementwise kernels run on one thread
     return 1
@@ -359,17 +373,7 @@ def main():
     e2e_rate = (re1 - re0) / e2e_s
 
     sec = ms / 1000.0
-    if dist:
-        tt = torch.tensor([sec, float(n_rhs)], device="cuda", dtype=torch.float64)
-        mx = tt.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        sec_all, rhs_all = float(mx[0]), float(tt[1])
-        e = torch.tensor([e2e_rate], device="cuda", dtype=torch.float64)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        e2e_all = float(e[0])
-    else:
-        sec_all, rhs_all, e2e_all = sec, float(n_rhs), e2e_rate
+    sec_all, rhs_all, e2e_all = combine_ranks(dist, sec, n_rhs, e2e_rate, "cuda")
 
     if rank == 0:
         peak, peak_kind = hbm_peak()
