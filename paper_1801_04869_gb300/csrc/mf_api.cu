@@ -4,6 +4,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "../../include/mf.h"
@@ -434,6 +436,74 @@ static mf_status ensure_h(mf_problem* pb, double t_target) {
   return MF_OK;
 }
 
+// CTAs per film of a shared launch: one each, then one at a time to the film with the most
+// transform work per CTA (cells x log2 cells) until the grid is full or every film has the
+// CTAs its own launch would use
+static std::vector<int> split_ctas(const std::vector<mf_problem*>& f, int total) {
+  const int n = (int)f.size();
+  std::vector<int> nb(n, 1);
+  std::vector<double> cost(n);
+  std::priority_queue<std::pair<double, int>> q;
+  for (int i = 0; i < n; ++i) {
+    const double c = (double)f[i]->d.nx * (double)f[i]->d.ny;
+    cost[i] = c * std::log2(c);
+    if (nb[i] < f[i]->d.grid) q.push({cost[i], i});
+  }
+  for (int used = n; used < total && !q.empty(); ++used) {
+    const int i = q.top().second;
+    q.pop();
+    ++nb[i];
+    if (nb[i] < f[i]->d.grid) q.push({cost[i] / nb[i], i});
+  }
+  return nb;
+}
+
+// Advance the films pbs[idx[k]] (one device, one precision) in shared persistent launches of
+// up to MAX_BATCH films, on the first film's stream; statuses go to st[idx[k]].
+static void advance_films_together(mf_problem* const* pbs, const std::vector<int>& idx,
+                                   const double* t_targets, long long max_attempts,
+                                   std::vector<mf_status>& st) {
+  mf_problem* p0 = pbs[idx[0]];
+  auto fail_all = [&](size_t k0, size_t k1, cudaError_t e, const char* what) {
+    for (size_t k = k0; k < k1; ++k) st[idx[k]] = cuda_fail(pbs[idx[k]], e, what);
+  };
+  cudaError_t e = cudaSetDevice(p0->device);
+  if (e != cudaSuccess) { fail_all(0, idx.size(), e, "cudaSetDevice"); return; }
+  const int prec = p0->d.precision;
+  const int per_sm = film_batch_max_blocks(prec, kernel_smem_bytes(p0->d));
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p0->device);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || per_sm < 1 || nsm < 1) {
+    fail_all(0, idx.size(), e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "shared launch configuration");
+    return;
+  }
+  const int coresident = per_sm * nsm;
+  const size_t chunk = (size_t)std::min(MAX_BATCH, coresident);
+  const cudaStream_t s = p0->stream;
+  BatchTable tab;           // 8 KB, copied into the launch's parameters
+  for (size_t k0 = 0; k0 < idx.size(); k0 += chunk) {
+    const size_t k1 = std::min(idx.size(), k0 + chunk);
+    std::vector<mf_problem*> f;
+    for (size_t k = k0; k < k1; ++k) f.push_back(pbs[idx[k]]);
+    const std::vector<int> nb = split_ctas(f, coresident);
+    tab.n = (int)f.size();
+    int b = 0;
+    e = cudaSuccess;
+    for (size_t j = 0; j < f.size() && e == cudaSuccess; ++j) {
+      // work already queued on the film's own stream comes first
+      e = cudaStreamSynchronize(f[j]->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(f[j]->d.gb, 0, sizeof(GridBarrier), s);
+      tab.job[j] = BatchJob{f[j]->d.dev, t_targets[idx[k0 + j]], max_attempts, b, nb[j]};
+      b += nb[j];
+    }
+    if (e == cudaSuccess) e = film_batch_launch(prec, tab, b, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { fail_all(k0, k1, e, "shared persistent launch"); continue; }
+    for (size_t k = k0; k < k1; ++k) st[idx[k]] = launch_finish(pbs[idx[k]]);
+  }
+}
+
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {
   if (!pb) return MF_ERR_ARG;
   mf_status r = ensure_h(pb, t_target);
@@ -450,16 +520,31 @@ mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_target
     if (!pbs[i]) return MF_ERR_ARG;
   std::vector<mf_status> st(n, MF_OK);
   for (int i = 0; i < n; ++i) st[i] = ensure_h(pbs[i], t_targets[i]);
-  // all launches first, each on its problem's stream, then the waits
+  // films of one device and precision share persistent launches; bulk bodies get one launch
+  // each, all enqueued on their own streams before any is waited for
+  std::vector<char> grouped(n, 0);
   for (int i = 0; i < n; ++i) {
-    if (st[i] != MF_OK) continue;
+    if (grouped[i] || st[i] != MF_OK || pbs[i]->d.dim != 2) continue;
+    std::vector<int> idx;
+    for (int j = i; j < n; ++j)
+      if (!grouped[j] && st[j] == MF_OK && pbs[j]->d.dim == 2 && pbs[j]->device == pbs[i]->device &&
+          pbs[j]->d.precision == pbs[i]->d.precision) {
+        idx.push_back(j);
+        grouped[j] = 1;
+      }
+    advance_films_together(pbs, idx, t_targets, max_attempts, st);
+  }
+  std::vector<char> launched(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (grouped[i] || st[i] != MF_OK) continue;
     KernelArgs a{};
     a.mode = MODE_ADVANCE; a.t_target = t_targets[i]; a.max_attempts = max_attempts;
     st[i] = launch_enqueue(pbs[i], a);
+    launched[i] = st[i] == MF_OK;
   }
   mf_status first = MF_OK;
   for (int i = 0; i < n; ++i) {
-    if (st[i] == MF_OK) st[i] = launch_finish(pbs[i]);
+    if (launched[i]) st[i] = launch_finish(pbs[i]);
     if (statuses) statuses[i] = st[i];
     if (first == MF_OK) first = st[i];
   }

@@ -336,8 +336,25 @@ struct KernelArgs {
   int seg;                    // waveform segment for MODE_RHS (-2: from t)
 };
 
+// One film of a shared launch (film_batch_kernel): CTAs [b0, b0 + nb) of the launch advance
+// it, with the film's own grid barrier, items and partials; nothing is shared between films.
+struct BatchJob {
+  const Desc* desc;           // the film's descriptor (device memory)
+  double t_target;
+  long long max_attempts;
+  int b0, nb;
+};
+constexpr int MAX_BATCH = 256;
+// passed by value as the kernel parameter (8 KB, under the 32 KB parameter limit)
+struct BatchTable {
+  int n;
+  BatchJob job[MAX_BATCH];
+};
+
 // launch helpers implemented next to each kernel
 cudaError_t film_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s);
+cudaError_t film_batch_launch(int precision, const BatchTable& tab, int grid, cudaStream_t s);
+int film_batch_max_blocks(int precision, size_t smem);
 cudaError_t bulk_launch(int precision, const Desc& d, const KernelArgs& a, cudaStream_t s);
 int film_max_blocks(int precision, size_t smem);
 int bulk_max_blocks(int precision, size_t smem);

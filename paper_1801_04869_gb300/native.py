@@ -281,9 +281,9 @@ def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int 
 
 
 def advance_batch(problems, t_targets, max_attempts: int = 1 << 40):
-    """mf_advance_batch: advance several problems together, each launched on its own stream
-    before any is waited for.  Returns the list of per-problem status codes; raises on the first
-    failure like the single-problem calls."""
+    """mf_advance_batch: advance several problems together (films of one precision in shared
+    persistent launches, bulk bodies one launch each).  Returns the list of per-problem status
+    codes; raises on the first failure like the single-problem calls."""
     lib = load()
     n = len(problems)
     hs = (ctypes.c_void_p * n)(*[p.h for p in problems])

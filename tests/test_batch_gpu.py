@@ -1,5 +1,6 @@
-"""mf_advance_batch: several films advanced together on their own streams give exactly the
-states of the same films advanced one at a time (the kernels are deterministic)."""
+"""mf_advance_batch: films advanced together in one shared persistent launch (each on its own
+range of CTAs) give exactly the states of the same films advanced one at a time: the items and
+the order of every reduction do not depend on how many CTAs run a film."""
 import numpy as np
 import pytest
 
@@ -21,10 +22,8 @@ def _state(p, n):
     return t, h, y
 
 
-def test_batch_equals_one_at_a_time():
-    wls = W.film_batch(4, seed=7, max_side=96, precision=1)
-    t_end = [0.05, 0.08, 0.05, 0.1]
-    batch = [native.from_workload(wl, stream=torch.cuda.Stream()) for wl in wls]
+def _check_equal_to_one_at_a_time(wls, t_end, streams=True):
+    batch = [native.from_workload(wl, stream=torch.cuda.Stream() if streams else None) for wl in wls]
     for p in batch:
         p.mf_set_state(0.0, None, h=1e-3)
     st = native.advance_batch(batch, t_end)
@@ -33,7 +32,7 @@ def test_batch_equals_one_at_a_time():
         ps = native.from_workload(wl)
         ps.mf_set_state(0.0, None, h=1e-3)
         ps.mf_advance(te)
-        n = wl.nx * wl.ny
+        n = wl.nx * wl.ny * wl.nz * (3 if wl.dim == 3 else 1)
         tb, hb, yb = _state(pb, n)
         ts, hs, ys = _state(ps, n)
         assert tb == ts == pytest.approx(te, abs=1e-12)
@@ -42,6 +41,28 @@ def test_batch_equals_one_at_a_time():
         ib, is_ = pb.mf_get_info(), ps.mf_get_info()
         for k in ("n_attempts", "n_rhs", "n_iters"):
             assert ib[k] == is_[k], k
+
+
+def test_batch_equals_one_at_a_time():
+    _check_equal_to_one_at_a_time(W.film_batch(4, seed=7, max_side=96, precision=1),
+                                  [0.05, 0.08, 0.05, 0.1])
+
+
+def test_mixed_batch_equals_one_at_a_time():
+    """Films of both precisions (one shared launch each) and a bulk cube (its own launch) in one
+    call, on one stream: each equals its one-at-a-time run."""
+    films = W.film_batch(5, seed=9, max_side=160, precision=1)
+    films[1].precision = 0
+    films[3].precision = 0
+    cube = W.cube_bulk(16, precision=1)
+    _check_equal_to_one_at_a_time(films + [cube], [0.04, 0.03, 0.05, 0.03, 0.04, 0.02], streams=False)
+
+
+def test_many_small_films_one_launch():
+    """40 films of 64..128 cells (grids 128^2 and 256^2): more films than fit one CTA range each
+    at their own launch widths, so every film runs on fewer CTAs than alone."""
+    wls = W.film_batch(40, seed=11, max_side=128, precision=1)
+    _check_equal_to_one_at_a_time(wls, [0.02] * len(wls), streams=False)
 
 
 def test_batch_reports_each_status():
