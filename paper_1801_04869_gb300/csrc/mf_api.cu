@@ -1,5 +1,6 @@
 // Host side of the C interface declared in include/mf.h: parameter checks, the workspace
 // layout, transform tables, and the launches of the persistent kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -436,72 +437,109 @@ static mf_status ensure_h(mf_problem* pb, double t_target) {
   return MF_OK;
 }
 
+// transform work of one pass over a film: cells x log2 cells
+static double film_cost(const mf_problem* p) {
+  const double c = (double)p->d.nx * (double)p->d.ny;
+  return c * std::log2(c);
+}
+
 // CTAs per film of a shared launch: one each, then one at a time to the film with the most
-// transform work per CTA (cells x log2 cells) until the grid is full or every film has the
-// CTAs its own launch would use
+// work per CTA until the grid is full or every film has the CTAs its own launch would use
+// (this minimises the largest work per CTA, which sets how long the launch lasts)
 static std::vector<int> split_ctas(const std::vector<mf_problem*>& f, int total) {
   const int n = (int)f.size();
   std::vector<int> nb(n, 1);
-  std::vector<double> cost(n);
   std::priority_queue<std::pair<double, int>> q;
-  for (int i = 0; i < n; ++i) {
-    const double c = (double)f[i]->d.nx * (double)f[i]->d.ny;
-    cost[i] = c * std::log2(c);
-    if (nb[i] < f[i]->d.grid) q.push({cost[i], i});
-  }
+  for (int i = 0; i < n; ++i)
+    if (nb[i] < f[i]->d.grid) q.push({film_cost(f[i]), i});
   for (int used = n; used < total && !q.empty(); ++used) {
     const int i = q.top().second;
     q.pop();
     ++nb[i];
-    if (nb[i] < f[i]->d.grid) q.push({cost[i] / nb[i], i});
+    if (nb[i] < f[i]->d.grid) q.push({film_cost(f[i]) / nb[i], i});
   }
   return nb;
 }
 
-// Advance the films pbs[idx[k]] (one device, one precision) in shared persistent launches of
-// up to MAX_BATCH films, on the first film's stream; statuses go to st[idx[k]].
+// Advance the films pbs[idx[k]] (one device, one precision); statuses go to st[idx[k]].  A film
+// whose own launch fills the GPU gets that launch (on its own stream): on a few CTAs of a
+// shared launch it would run slower than alone, and it would set how long the shared launch
+// lasts.  The other films share persistent launches on the first film's stream, largest
+// first; a launch is closed before a film whose share of the grid (in proportion to its work)
+// would be less than one CTA, so films of very different sizes run in successive launches
+// instead of the small ones idling beside large ones squeezed onto single CTAs.
 static void advance_films_together(mf_problem* const* pbs, const std::vector<int>& idx,
                                    const double* t_targets, long long max_attempts,
                                    std::vector<mf_status>& st) {
   mf_problem* p0 = pbs[idx[0]];
-  auto fail_all = [&](size_t k0, size_t k1, cudaError_t e, const char* what) {
-    for (size_t k = k0; k < k1; ++k) st[idx[k]] = cuda_fail(pbs[idx[k]], e, what);
-  };
   cudaError_t e = cudaSetDevice(p0->device);
-  if (e != cudaSuccess) { fail_all(0, idx.size(), e, "cudaSetDevice"); return; }
+  if (e != cudaSuccess) {
+    for (int i : idx) st[i] = cuda_fail(pbs[i], e, "cudaSetDevice");
+    return;
+  }
   const int prec = p0->d.precision;
   const int per_sm = film_batch_max_blocks(prec, kernel_smem_bytes(p0->d));
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p0->device);
   e = cudaGetLastError();
   if (e != cudaSuccess || per_sm < 1 || nsm < 1) {
-    fail_all(0, idx.size(), e != cudaSuccess ? e : cudaErrorInvalidConfiguration, "shared launch configuration");
+    if (e == cudaSuccess) e = cudaErrorInvalidConfiguration;
+    for (int i : idx) st[i] = cuda_fail(pbs[i], e, "shared launch configuration");
     return;
   }
   const int coresident = per_sm * nsm;
-  const size_t chunk = (size_t)std::min(MAX_BATCH, coresident);
-  const cudaStream_t s = p0->stream;
-  BatchTable tab;           // 8 KB, copied into the launch's parameters
-  for (size_t k0 = 0; k0 < idx.size(); k0 += chunk) {
-    const size_t k1 = std::min(idx.size(), k0 + chunk);
+  const size_t cap = (size_t)std::min(MAX_BATCH, coresident);
+  // work already queued on the films' own streams comes first
+  for (int i : idx) {
+    e = cudaStreamSynchronize(pbs[i]->stream);
+    if (e != cudaSuccess) st[i] = cuda_fail(pbs[i], e, "cudaStreamSynchronize");
+  }
+  std::vector<int> order, alone;
+  for (int i : idx) {
+    if (st[i] != MF_OK) continue;
+    if (pbs[i]->d.grid < coresident) {
+      order.push_back(i);
+      continue;
+    }
+    KernelArgs a{};
+    a.mode = MODE_ADVANCE; a.t_target = t_targets[i]; a.max_attempts = max_attempts;
+    st[i] = launch_enqueue(pbs[i], a);
+    if (st[i] == MF_OK) alone.push_back(i);
+  }
+  const cudaStream_t s = order.empty() ? p0->stream : pbs[order[0]]->stream;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return film_cost(pbs[a]) > film_cost(pbs[b]); });
+  std::vector<int> launched;
+  BatchTable tab;           // 8 KB, copied into each launch's parameters
+  for (size_t k0 = 0; k0 < order.size();) {
+    double sum = film_cost(pbs[order[k0]]);
+    size_t k1 = k0 + 1;
+    for (; k1 < order.size() && k1 - k0 < cap; ++k1) {
+      const double c = film_cost(pbs[order[k1]]);
+      if (sum + c > (double)coresident * c) break;
+      sum += c;
+    }
     std::vector<mf_problem*> f;
-    for (size_t k = k0; k < k1; ++k) f.push_back(pbs[idx[k]]);
+    for (size_t k = k0; k < k1; ++k) f.push_back(pbs[order[k]]);
     const std::vector<int> nb = split_ctas(f, coresident);
     tab.n = (int)f.size();
     int b = 0;
     e = cudaSuccess;
     for (size_t j = 0; j < f.size() && e == cudaSuccess; ++j) {
-      // work already queued on the film's own stream comes first
-      e = cudaStreamSynchronize(f[j]->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(f[j]->d.gb, 0, sizeof(GridBarrier), s);
-      tab.job[j] = BatchJob{f[j]->d.dev, t_targets[idx[k0 + j]], max_attempts, b, nb[j]};
+      e = cudaMemsetAsync(f[j]->d.gb, 0, sizeof(GridBarrier), s);
+      tab.job[j] = BatchJob{f[j]->d.dev, t_targets[order[k0 + j]], max_attempts, b, nb[j]};
       b += nb[j];
     }
     if (e == cudaSuccess) e = film_batch_launch(prec, tab, b, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { fail_all(k0, k1, e, "shared persistent launch"); continue; }
-    for (size_t k = k0; k < k1; ++k) st[idx[k]] = launch_finish(pbs[idx[k]]);
+    for (size_t k = k0; k < k1; ++k) {
+      if (e == cudaSuccess) launched.push_back(order[k]);
+      else st[order[k]] = cuda_fail(pbs[order[k]], e, "shared persistent launch");
+    }
+    k0 = k1;
   }
+  e = launched.empty() ? cudaSuccess : cudaStreamSynchronize(s);
+  for (int i : launched) st[i] = e == cudaSuccess ? launch_finish(pbs[i]) : cuda_fail(pbs[i], e, "shared persistent launch");
+  for (int i : alone) st[i] = launch_finish(pbs[i]);
 }
 
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {

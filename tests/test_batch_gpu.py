@@ -48,14 +48,18 @@ def test_batch_equals_one_at_a_time():
                                   [0.05, 0.08, 0.05, 0.1])
 
 
-def test_mixed_batch_equals_one_at_a_time():
-    """Films of both precisions (one shared launch each) and a bulk cube (its own launch) in one
-    call, on one stream: each equals its one-at-a-time run."""
+@pytest.mark.parametrize("streams", [False, True])
+def test_mixed_batch_equals_one_at_a_time(streams):
+    """Films of both precisions (shared launches per precision), a 1024^2 film whose own launch
+    fills the GPU (launched alone) and a bulk cube (its own launch) in one call: each equals its
+    one-at-a-time run."""
     films = W.film_batch(5, seed=9, max_side=160, precision=1)
     films[1].precision = 0
     films[3].precision = 0
+    big = W.rect_film_2048(precision=1, n_grid=1024)
     cube = W.cube_bulk(16, precision=1)
-    _check_equal_to_one_at_a_time(films + [cube], [0.04, 0.03, 0.05, 0.03, 0.04, 0.02], streams=False)
+    _check_equal_to_one_at_a_time([big] + films + [cube], [0.005, 0.04, 0.03, 0.05, 0.03, 0.04, 0.02],
+                                  streams=streams)
 
 
 def test_many_small_films_one_launch():
