@@ -185,6 +185,24 @@ def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 12
                          "bytes_model": f"(60 + 60 I) M3 per RHS, M3 = {n_grid}^3 x 4 B"}}
 
 
+def autotune_leg(native, W, torch, n_grid: int):
+    """Secondary line: mf_autotune on the benchmark film (a separate problem object): the
+    work-item shapes and launch widths it timed and the one it keeps, against the size rules'
+    choice that the timed region uses."""
+    wl = W.rect_film_2048(precision=1, n_grid=n_grid)
+    p = native.from_workload(wl)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    p.mf_set_state(0.05, torch.as_tensor(g0, device="cuda"), h=2e-5)
+    default = p.mf_get_info()
+    tu = p.mf_autotune(reps=5, force_iters=4)
+    return {"workload": wl.name, "candidates": tu["candidates"],
+            "default": {"rows_per_item": default["rows_per_item"], "grid": default["grid"],
+                        "ms_per_rhs": tu["ms_per_rhs_default"]},
+            "chosen": {"rows_per_item": tu["rows_per_item"], "two_field_rows": tu["zs_per_item"],
+                       "grid": tu["grid"], "ms_per_rhs": tu["ms_per_rhs"]},
+            "timing": "CUDA events, 5 launches of one right-hand side with 4 forced outside iterations"}
+
+
 def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 2):
     """Secondary line: a sweep of `count` independent films (seeded shapes, sides 64..512 cells,
     grids twice the film, n in {19, 30, 50}, ramp amplitudes in [0.2, 1]), FP32 transforms,
@@ -412,6 +430,8 @@ def main():
                              f"({el:.1f} s on the host)"}
         info = p.mf_get_info()
         bulk = bulk_leg(native, W, torch) if not args.no_extra else None
+        bulk_256 = bulk_leg(native, W, torch, n_grid=256) if not args.no_extra else None
+        tune = autotune_leg(native, W, torch, args.grid) if not args.no_extra else None
         batch = batch_leg(native, W, torch) if not args.no_extra else None
         ramps = [full_ramp_leg(native, W, torch, prec) for prec in (0, 1)] if not args.no_extra else None
         line = {
@@ -442,6 +462,8 @@ def main():
             "gpu_launches": 1,
             "clocks": ck.summary(),
             "bulk": bulk,
+            "bulk_256": bulk_256,
+            "autotune": tune,
             "batch": batch,
             "full_ramp": ramps,
         }

@@ -180,6 +180,27 @@ mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, d
 /* Counters, state and launch configuration. */
 mf_status mf_get_info(mf_problem* pb, mf_info* out);
 
+/* Result of mf_autotune. */
+typedef struct {
+  int rows_per_item;          /* rows of the film row passes / bulk x pass per work item */
+  int zs_per_item;            /* bulk y pass z-lines per item (films: two-field row pass rows) */
+  int grid;                   /* CTAs of the persistent launch */
+  int candidates;             /* configurations timed */
+  double ms_per_rhs;          /* best time of one right-hand side with the forced iterations */
+  double ms_per_rhs_default;  /* the same for the configuration chosen at mf_create */
+} mf_tuning;
+
+/* Time one right-hand side of the current state (force_iters outside iterations, reps timed
+   launches after one warm-up) for every work-item shape and launch width the kernels accept
+   for this grid, and keep the fastest; *out (may be NULL) receives it.  The candidates are the
+   power-of-two rows (and z-lines) per item that fit the shared-memory batch, times the launch
+   widths {size rule, all co-resident CTAs, half of them}.  Results change at rounding level
+   with the item shape (the reductions are summed per item), not with the launch width.  The
+   state, step size and counters are kept; the warm start of the outside iteration and the
+   first-same-as-last derivative are cleared (as mf_reset_warm and mf_set_state do).  The
+   tuning has no counterpart in the paper: it adapts the FFT passes' tiling to the grid. */
+mf_status mf_autotune(mf_problem* pb, int reps, int force_iters, mf_tuning* out);
+
 /* Copy up to cap logged step attempts (host memory); *count gets the number logged. */
 mf_status mf_get_log(mf_problem* pb, mf_step_log* out, long long cap, long long* count);
 

@@ -1,6 +1,7 @@
 // Host side of the C interface declared in include/mf.h: parameter checks, the workspace
 // layout, transform tables, and the launches of the persistent kernels.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -647,6 +648,114 @@ mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_
     }
   }
   return MF_OK;
+}
+
+// work-item shapes and launch widths the persistent kernels accept for this problem
+static std::vector<std::array<int, 3>> tuning_candidates(const mf_problem* pb, int coresident) {
+  const Desc& d = pb->d;
+  std::vector<std::array<int, 3>> c;
+  std::vector<int> grids = {d.grid, coresident, coresident / 2};
+  std::sort(grids.begin(), grids.end());
+  grids.erase(std::unique(grids.begin(), grids.end()), grids.end());
+  auto add = [&](int rb, int zs) {
+    for (int g : grids)
+      if (g >= 1 && g <= coresident) c.push_back({rb, zs, g});
+  };
+  if (d.dim == 2) {
+    // row passes: rb one-field rows (and min(rb, BATCH / nx) two-field rows) per item
+    const int rb_max = std::min(d.ny, 2 * BATCH / d.nx);
+    for (int rb = 2; rb <= rb_max; rb *= 2) add(rb, std::max(2, std::min(rb, BATCH / d.nx)));
+  } else {
+    // x pass: rb rows of 3 fields; y pass: zs z-lines of 3 fields
+    for (int rb = 2; rb <= d.ny && 3 * d.nx * (rb / 2) <= BATCH; rb *= 2)
+      for (int zs = 1; zs <= d.nz && 3 * d.ny * zs <= BATCH; zs *= 2) add(rb, zs);
+  }
+  return c;
+}
+
+mf_status mf_autotune(mf_problem* pb, int reps, int force_iters, mf_tuning* out) {
+  if (!pb || reps < 1 || force_iters < 1) return MF_ERR_ARG;
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  SolverState s0;
+  mf_status r = read_state(pb, &s0);
+  if (r != MF_OK) return r;
+  const int per_sm = pb->d.dim == 2 ? film_max_blocks(pb->d.precision, kernel_smem_bytes(pb->d))
+                                    : bulk_max_blocks(pb->d.precision, kernel_smem_bytes(pb->d));
+  int nsm = 0;
+  MF_CUDA(pb, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pb->device));
+  if (per_sm < 1 || nsm < 1) { pb->err = "kernel does not fit on this device"; return MF_ERR_CUDA; }
+  const Desc base = pb->d;
+  const std::vector<std::array<int, 3>> cand = tuning_candidates(pb, per_sm * nsm);
+  // right-hand sides of the current state into a buffer the state does not use
+  KernelArgs a{};
+  a.mode = MODE_RHS; a.t = s0.t; a.seg = -2; a.force_iters = force_iters;
+  a.y_in = base.fbuf[s0.ybuf];
+  a.out = base.fbuf[(s0.ybuf + 1) % 6];
+  cudaEvent_t e0, e1;
+  MF_CUDA(pb, cudaEventCreate(&e0));
+  MF_CUDA(pb, cudaEventCreate(&e1));
+  auto upload = [&](const Desc& d) {
+    cudaError_t e = cudaMemcpyAsync((void*)d.dev, &d, sizeof(Desc), cudaMemcpyHostToDevice, pb->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(pb->stream) : e;   // the host copy is a local
+  };
+  double best = 0.0, dflt = 0.0;
+  size_t ibest = cand.size();
+  for (size_t i = 0; i < cand.size() && r == MF_OK; ++i) {
+    pb->d = base;
+    pb->d.rows_per_item = cand[i][0];
+    pb->d.zs_per_item = cand[i][1];
+    pb->d.grid = cand[i][2];
+    cudaError_t e = upload(pb->d);
+    if (e != cudaSuccess) { r = cuda_fail(pb, e, "descriptor upload"); break; }
+    // forced iterations may end above the tolerance (MF_ERR_NOCONV): the timing is what counts
+    r = launch(pb, a);                                   // warm-up
+    if (r == MF_ERR_NOCONV) r = MF_OK;
+    for (int k = 0; k <= reps && r == MF_OK; ++k) {
+      if (k == 0) e = cudaEventRecord(e0, pb->stream);
+      else r = launch_enqueue(pb, a);
+      if (k == reps && r == MF_OK) e = cudaEventRecord(e1, pb->stream);
+      if (e != cudaSuccess) r = cuda_fail(pb, e, "cudaEventRecord");
+    }
+    if (r == MF_OK) r = launch_finish(pb);
+    if (r == MF_ERR_NOCONV) r = MF_OK;
+    float ms = 0.f;
+    if (r == MF_OK) {
+      e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) r = cuda_fail(pb, e, "cudaEventElapsedTime");
+    }
+    if (r != MF_OK) break;
+    const double per = (double)ms / reps;
+    const bool is_default = cand[i][0] == base.rows_per_item && cand[i][1] == base.zs_per_item &&
+                            cand[i][2] == base.grid;
+    if (is_default) dflt = per;
+    if (ibest == cand.size() || per < best) { best = per; ibest = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pb->d = base;
+  if (r == MF_OK && ibest < cand.size()) {
+    pb->d.rows_per_item = cand[ibest][0];
+    pb->d.zs_per_item = cand[ibest][1];
+    pb->d.grid = cand[ibest][2];
+  }
+  cudaError_t e = upload(pb->d);
+  if (e != cudaSuccess && r == MF_OK) r = cuda_fail(pb, e, "descriptor upload");
+  // the state, step size and counters as they were; the tuning runs overwrote the outside
+  // iteration's warm start and a derivative buffer
+  SolverState s1 = s0;
+  s1.k1_valid = 0;
+  s1.warm_valid = 0; s1.A_prev = 0.0; s1.com_valid = 0; s1.hd_sel = 0; s1.A_com = 0.0;
+  const mf_status w = write_state(pb, &s1);
+  if (r == MF_OK) r = w;
+  if (r == MF_OK && out) {
+    out->rows_per_item = pb->d.rows_per_item;
+    out->zs_per_item = pb->d.zs_per_item;
+    out->grid = pb->d.grid;
+    out->candidates = (int)cand.size();
+    out->ms_per_rhs = best;
+    out->ms_per_rhs_default = dflt;
+  }
+  return r;
 }
 
 mf_status mf_get_info(mf_problem* pb, mf_info* out) {

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_NOCONV
 EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf_rhs_ex",
            "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
-           "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch"]
+           "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
+           "mf_autotune"]
 
 
 class mf_params(ctypes.Structure):
@@ -62,6 +63,12 @@ class mf_info(ctypes.Structure):
                 ("rows_per_item", ctypes.c_int), ("workspace_used", ctypes.c_longlong)]
 
 
+class mf_tuning(ctypes.Structure):
+    _fields_ = [("rows_per_item", ctypes.c_int), ("zs_per_item", ctypes.c_int),
+                ("grid", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("ms_per_rhs", ctypes.c_double), ("ms_per_rhs_default", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -92,6 +99,7 @@ def load() -> ctypes.CDLL:
         "mf_readout": (ctypes.c_int, [vp, ctypes.c_int, vp]),
         "mf_readout_of": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, vp, vp]),
         "mf_get_info": (ctypes.c_int, [vp, P(mf_info)]),
+        "mf_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, P(mf_tuning)]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -244,6 +252,12 @@ class Problem:
         inf = mf_info()
         self._check(self.lib.mf_get_info(self.h, ctypes.byref(inf)))
         return {name: getattr(inf, name) for name, _ in mf_info._fields_}
+
+    def mf_autotune(self, reps: int = 3, force_iters: int = 2) -> dict:
+        """Time the accepted work-item shapes and launch widths and keep the fastest."""
+        tu = mf_tuning()
+        self._check(self.lib.mf_autotune(self.h, reps, force_iters, ctypes.byref(tu)))
+        return {name: getattr(tu, name) for name, _ in mf_tuning._fields_}
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()

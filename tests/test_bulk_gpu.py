@@ -109,6 +109,15 @@ def test_rhs_full_size_cube_128_fp32():
     _rhs_pair(wl, h, [0.2], force=2, tol=TOL32)
 
 
+@pytest.mark.slow
+def test_rhs_full_size_cube_256_fp32():
+    """The larger cube workload (128^3 cells in a 256^3 grid), FP32 transforms, against the FP64
+    oracle (one forced outside iteration: the oracle takes about half a minute)."""
+    wl = W.cube_bulk(256, precision=1)
+    h = W.bulk_state(wl.mask, (1.0, 1.0, 1.0), seed=46)
+    _rhs_pair(wl, h, [0.2], force=1, tol=TOL32)
+
+
 def test_ramp_fp64_lock_step_small_cube():
     """Cube 16^3 cells in a 32^3 grid through the ramp knot at t = 0.5, replayed by the oracle."""
     wl = W.cube_bulk(32, precision=0)
