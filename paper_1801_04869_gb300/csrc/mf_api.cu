@@ -439,36 +439,34 @@ static mf_status ensure_h(mf_problem* pb, double t_target) {
 }
 
 // transform work of one pass over a film: cells x log2 cells
-static double film_cost(const mf_problem* p) {
-  const double c = (double)p->d.nx * (double)p->d.ny;
+static double film_cost(int nx, int ny) {
+  const double c = (double)nx * (double)ny;
   return c * std::log2(c);
 }
 
 // CTAs per film of a shared launch: one each, then one at a time to the film with the most
 // work per CTA until the grid is full or every film has the CTAs its own launch would use
 // (this minimises the largest work per CTA, which sets how long the launch lasts)
-static std::vector<int> split_ctas(const std::vector<mf_problem*>& f, int total) {
-  const int n = (int)f.size();
-  std::vector<int> nb(n, 1);
+static void split_ctas(const int* nx, const int* ny, const int* own, const int* films, int n,
+                       int total, int* ctas) {
   std::priority_queue<std::pair<double, int>> q;
-  for (int i = 0; i < n; ++i)
-    if (nb[i] < f[i]->d.grid) q.push({film_cost(f[i]), i});
-  for (int used = n; used < total && !q.empty(); ++used) {
-    const int i = q.top().second;
-    q.pop();
-    ++nb[i];
-    if (nb[i] < f[i]->d.grid) q.push({film_cost(f[i]) / nb[i], i});
+  for (int k = 0; k < n; ++k) {
+    const int i = films[k];
+    ctas[i] = 1;
+    if (ctas[i] < own[i]) q.push({film_cost(nx[i], ny[i]), k});
   }
-  return nb;
+  for (int used = n; used < total && !q.empty(); ++used) {
+    const int i = films[q.top().second];
+    const int k = q.top().second;
+    q.pop();
+    ++ctas[i];
+    if (ctas[i] < own[i]) q.push({film_cost(nx[i], ny[i]) / ctas[i], k});
+  }
 }
 
-// Advance the films pbs[idx[k]] (one device, one precision); statuses go to st[idx[k]].  A film
-// whose own launch fills the GPU gets that launch (on its own stream): on a few CTAs of a
-// shared launch it would run slower than alone, and it would set how long the shared launch
-// lasts.  The other films share persistent launches on the first film's stream, largest
-// first; a launch is closed before a film whose share of the grid (in proportion to its work)
-// would be less than one CTA, so films of very different sizes run in successive launches
-// instead of the small ones idling beside large ones squeezed onto single CTAs.
+// Advance the films pbs[idx[k]] (one device, one precision) as mf_batch_plan arranges them;
+// statuses go to st[idx[k]].  Shared launches go on the first shared film's stream, one after
+// the other; films with a launch of their own go on their own streams.
 static void advance_films_together(mf_problem* const* pbs, const std::vector<int>& idx,
                                    const double* t_targets, long long max_attempts,
                                    std::vector<mf_status>& st) {
@@ -488,59 +486,93 @@ static void advance_films_together(mf_problem* const* pbs, const std::vector<int
     for (int i : idx) st[i] = cuda_fail(pbs[i], e, "shared launch configuration");
     return;
   }
-  const int coresident = per_sm * nsm;
-  const size_t cap = (size_t)std::min(MAX_BATCH, coresident);
   // work already queued on the films' own streams comes first
+  std::vector<int> live;
   for (int i : idx) {
     e = cudaStreamSynchronize(pbs[i]->stream);
     if (e != cudaSuccess) st[i] = cuda_fail(pbs[i], e, "cudaStreamSynchronize");
+    else live.push_back(i);
   }
-  std::vector<int> order, alone;
-  for (int i : idx) {
-    if (st[i] != MF_OK) continue;
-    if (pbs[i]->d.grid < coresident) {
-      order.push_back(i);
-      continue;
-    }
+  const int n = (int)live.size();
+  if (n == 0) return;
+  std::vector<int> nx(n), ny(n), own(n), order(n), launch(n), ctas(n);
+  for (int k = 0; k < n; ++k) {
+    nx[k] = pbs[live[k]]->d.nx; ny[k] = pbs[live[k]]->d.ny; own[k] = pbs[live[k]]->d.grid;
+  }
+  const int nlaunch = mf_batch_plan(n, nx.data(), ny.data(), own.data(), per_sm * nsm,
+                                    order.data(), launch.data(), ctas.data());
+  std::vector<int> alone, shared;
+  for (int k : order) {
+    const int i = live[k];
+    if (launch[k] >= 0) continue;
     KernelArgs a{};
     a.mode = MODE_ADVANCE; a.t_target = t_targets[i]; a.max_attempts = max_attempts;
     st[i] = launch_enqueue(pbs[i], a);
     if (st[i] == MF_OK) alone.push_back(i);
   }
-  const cudaStream_t s = order.empty() ? p0->stream : pbs[order[0]]->stream;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return film_cost(pbs[a]) > film_cost(pbs[b]); });
-  std::vector<int> launched;
+  cudaStream_t s = p0->stream;
+  for (int k : order)
+    if (launch[k] >= 0) { s = pbs[live[k]]->stream; break; }
   BatchTable tab;           // 8 KB, copied into each launch's parameters
-  for (size_t k0 = 0; k0 < order.size();) {
-    double sum = film_cost(pbs[order[k0]]);
+  for (int j = 0; j < nlaunch; ++j) {
+    std::vector<int> members;
+    tab.n = 0;
+    int b = 0;
+    e = cudaSuccess;
+    for (int k : order) {
+      if (launch[k] != j) continue;
+      mf_problem* f = pbs[live[k]];
+      if (e == cudaSuccess) e = cudaMemsetAsync(f->d.gb, 0, sizeof(GridBarrier), s);
+      tab.job[tab.n++] = BatchJob{f->d.dev, t_targets[live[k]], max_attempts, b, ctas[k]};
+      b += ctas[k];
+      members.push_back(live[k]);
+    }
+    if (e == cudaSuccess) e = film_batch_launch(prec, tab, b, s);
+    for (int i : members) {
+      if (e == cudaSuccess) shared.push_back(i);
+      else st[i] = cuda_fail(pbs[i], e, "shared persistent launch");
+    }
+  }
+  e = shared.empty() ? cudaSuccess : cudaStreamSynchronize(s);
+  for (int i : shared) st[i] = e == cudaSuccess ? launch_finish(pbs[i]) : cuda_fail(pbs[i], e, "shared persistent launch");
+  for (int i : alone) st[i] = launch_finish(pbs[i]);
+}
+
+int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid,
+                             int coresident, int* order, int* launch, int* ctas) {
+  if (n < 0 || (n > 0 && (!nx || !ny || !own_grid || !order || !launch || !ctas)) || coresident < 1)
+    return -1;
+  for (int i = 0; i < n; ++i)
+    if (nx[i] < 1 || ny[i] < 1 || own_grid[i] < 1) return -1;
+  for (int i = 0; i < n; ++i) order[i] = i;
+  // largest first (stable: equal films keep their order)
+  std::stable_sort(order, order + n, [&](int a, int b) {
+    return film_cost(nx[a], ny[a]) > film_cost(nx[b], ny[b]);
+  });
+  // films whose own launch fills the GPU keep it
+  std::vector<int> sh;
+  for (int k = 0; k < n; ++k) {
+    const int i = order[k];
+    if (own_grid[i] >= coresident) { launch[i] = -1; ctas[i] = coresident; }
+    else sh.push_back(i);
+  }
+  // the others fill shared launches, largest first; a launch is closed before a film whose
+  // share of the grid in proportion to its work would be below one CTA
+  const size_t cap = (size_t)std::min(MAX_BATCH, coresident);
+  int nl = 0;
+  for (size_t k0 = 0; k0 < sh.size(); ++nl) {
+    double sum = film_cost(nx[sh[k0]], ny[sh[k0]]);
     size_t k1 = k0 + 1;
-    for (; k1 < order.size() && k1 - k0 < cap; ++k1) {
-      const double c = film_cost(pbs[order[k1]]);
+    for (; k1 < sh.size() && k1 - k0 < cap; ++k1) {
+      const double c = film_cost(nx[sh[k1]], ny[sh[k1]]);
       if (sum + c > (double)coresident * c) break;
       sum += c;
     }
-    std::vector<mf_problem*> f;
-    for (size_t k = k0; k < k1; ++k) f.push_back(pbs[order[k]]);
-    const std::vector<int> nb = split_ctas(f, coresident);
-    tab.n = (int)f.size();
-    int b = 0;
-    e = cudaSuccess;
-    for (size_t j = 0; j < f.size() && e == cudaSuccess; ++j) {
-      e = cudaMemsetAsync(f[j]->d.gb, 0, sizeof(GridBarrier), s);
-      tab.job[j] = BatchJob{f[j]->d.dev, t_targets[order[k0 + j]], max_attempts, b, nb[j]};
-      b += nb[j];
-    }
-    if (e == cudaSuccess) e = film_batch_launch(prec, tab, b, s);
-    for (size_t k = k0; k < k1; ++k) {
-      if (e == cudaSuccess) launched.push_back(order[k]);
-      else st[order[k]] = cuda_fail(pbs[order[k]], e, "shared persistent launch");
-    }
+    for (size_t k = k0; k < k1; ++k) launch[sh[k]] = nl;
+    split_ctas(nx, ny, own_grid, sh.data() + k0, (int)(k1 - k0), coresident, ctas);
     k0 = k1;
   }
-  e = launched.empty() ? cudaSuccess : cudaStreamSynchronize(s);
-  for (int i : launched) st[i] = e == cudaSuccess ? launch_finish(pbs[i]) : cuda_fail(pbs[i], e, "shared persistent launch");
-  for (int i : alone) st[i] = launch_finish(pbs[i]);
+  return nl;
 }
 
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {

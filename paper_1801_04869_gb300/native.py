@@ -27,7 +27,7 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
            "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
-           "mf_autotune"]
+           "mf_autotune", "mf_batch_plan"]
 
 
 class mf_params(ctypes.Structure):
@@ -100,6 +100,7 @@ def load() -> ctypes.CDLL:
         "mf_readout_of": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, vp, vp]),
         "mf_get_info": (ctypes.c_int, [vp, P(mf_info)]),
         "mf_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, P(mf_tuning)]),
+        "mf_batch_plan": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ctypes.c_int, ip, ip, ip]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -292,6 +293,18 @@ def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int 
                                  force_iters, ctypes.c_void_p(s.cuda_stream), ctypes.byref(it),
                                  msg, 256)
     return st, it.value, msg.value.decode()
+
+
+def batch_plan(nx, ny, own_grid, coresident: int):
+    """mf_batch_plan (host only): (number of shared launches, order, launch, ctas)."""
+    lib = load()
+    n = len(nx)
+    arr = lambda v: (ctypes.c_int * max(n, 1))(*[int(x) for x in v])
+    order, launch, ctas = arr([0] * n), arr([0] * n), arr([0] * n)
+    r = lib.mf_batch_plan(n, arr(nx), arr(ny), arr(own_grid), int(coresident), order, launch, ctas)
+    if r < 0:
+        raise ValueError("mf_batch_plan: invalid arguments")
+    return r, list(order)[:n], list(launch)[:n], list(ctas)[:n]
 
 
 def advance_batch(problems, t_targets, max_attempts: int = 1 << 40):
