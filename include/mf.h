@@ -142,18 +142,17 @@ mf_status mf_get_state(mf_problem* pb, double* t, double* h, double* d_y);
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts);
 
 /* Advance n independent problems (films or bulk bodies) to t_targets[i] (as mf_advance), at
-   the same time.  Films (dim 2) of one device and precision run in shared persistent
-   launches of up to 256 films, on the stream of the first of them: the launch's CTAs are cut
-   into one consecutive range per film (at least one CTA each, the rest by transform work,
-   never more than the film's own launch would use), and every range runs the one-film code
-   with that film's descriptor, grid barrier and partial sums, so each film's result is
-   identical to its mf_advance.  Work already queued on a film's own stream is waited for
-   before the launch.  Bulk bodies get one launch each on their own streams, all enqueued
-   before any is waited for.  Batching has no counterpart in the paper: it is how many
-   independent magnetization problems (a parameter or geometry sweep) share one GPU.
-   statuses (may be NULL) receives each problem's status; the return value is the first non-OK
-   one (MF_OK if all succeeded).  pbs must not repeat a problem.  Returns when every problem
-   has finished. */
+   the same time.  Films (dim 2) of one device and precision are arranged as mf_batch_plan
+   describes: a film whose own launch fills the GPU gets that launch, on its own stream; the
+   others share persistent launches, one after the other on the stream of the first of them,
+   each launch's CTAs cut into one consecutive range per film, and every range runs the
+   one-film code with that film's descriptor, grid barrier and partial sums, so each film's
+   result is identical to its mf_advance.  Work already queued on a film's own stream is waited
+   for first.  Bulk bodies get one launch each on their own streams, all enqueued before any is
+   waited for.  Batching has no counterpart in the paper: it is how many independent
+   magnetization problems (a parameter or geometry sweep) share one GPU.  statuses (may be
+   NULL) receives each problem's status; the return value is the first non-OK one (MF_OK if
+   all succeeded).  pbs must not repeat a problem.  Returns when every problem has finished. */
 mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_targets,
                            long long max_attempts, mf_status* statuses);
 
