@@ -192,6 +192,18 @@ mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, d
 /* Counters, state and launch configuration. */
 mf_status mf_get_info(mf_problem* pb, mf_info* out);
 
+/* Checkpoints: everything a continuation reads — the integrator state and counters, the six
+   FP64 state/derivative buffers (with the first-same-as-last derivative), the outside
+   iteration's warm start, the step log, and the work-item shape and launch width.  Restoring a
+   checkpoint into a problem created with the same parameters makes its next calls identical,
+   bit for bit, to the saved problem's.  The blob has mf_checkpoint_bytes bytes, in host or
+   device memory owned by the caller; save and restore run on the problem's stream and wait for
+   it.  Restore returns MF_ERR_ARG (and changes nothing) if the blob's grid, dimension or
+   precision differ.  Checkpoints have no counterpart in the paper. */
+size_t mf_checkpoint_bytes(const mf_problem* pb);
+mf_status mf_checkpoint_save(mf_problem* pb, void* dst);
+mf_status mf_checkpoint_restore(mf_problem* pb, const void* src);
+
 /* Result of mf_autotune. */
 typedef struct {
   int rows_per_item;          /* rows of the film row passes / bulk x pass per work item */

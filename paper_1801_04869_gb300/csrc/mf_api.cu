@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mf.h"
 #include "mf_common.cuh"
 #include "mf_tables.h"
@@ -30,6 +32,12 @@ struct mf_problem {
 };
 
 namespace {
+
+// NVTX range over one host call (shown by nsys / ncu timelines; free when no tool is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 constexpr long long LOG_CAP = 1 << 16;
 constexpr int NSLOTS = 8;
@@ -367,6 +375,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
 
 mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double* d_ydot,
                     int force_iters, int* iters_out) {
+  Range range_("mf_rhs");
   if (!pb || !d_y || !d_ydot) return MF_ERR_ARG;
   KernelArgs a{};
   a.mode = MODE_RHS; a.t = t; a.y_in = d_y; a.out = d_ydot; a.force_iters = force_iters; a.seg = seg;
@@ -576,6 +585,7 @@ int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid,
 }
 
 mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {
+  Range range_("mf_advance");
   if (!pb) return MF_ERR_ARG;
   mf_status r = ensure_h(pb, t_target);
   if (r != MF_OK) return r;
@@ -586,6 +596,7 @@ mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts) {
 
 mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_targets,
                            long long max_attempts, mf_status* statuses) {
+  Range range_("mf_advance_batch");
   if (!pbs || !t_targets || n < 0) return MF_ERR_ARG;
   for (int i = 0; i < n; ++i)
     if (!pbs[i]) return MF_ERR_ARG;
@@ -623,6 +634,7 @@ mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_target
 }
 
 mf_status mf_step(mf_problem* pb, double t_max, int* accepted) {
+  Range range_("mf_step");
   if (!pb) return MF_ERR_ARG;
   SolverState s0;
   mf_status r = read_state(pb, &s0);
@@ -664,6 +676,7 @@ mf_status mf_readout(mf_problem* pb, int what, double* out) {
 
 mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_m_out,
                       double* d_hz_out) {
+  Range range_("mf_run_ramp");
   if (!pb || n_out < 0 || (n_out > 0 && !t_out)) return MF_ERR_ARG;
   const int nm = pb->d.dim == 2 ? 1 : 3;
   const long long per = pb->d.dim == 2 ? pb->d.ncell : 3 * pb->d.ncell;
@@ -706,6 +719,7 @@ static std::vector<std::array<int, 3>> tuning_candidates(const mf_problem* pb, i
 }
 
 mf_status mf_autotune(mf_problem* pb, int reps, int force_iters, mf_tuning* out) {
+  Range range_("mf_autotune");
   if (!pb || reps < 1 || force_iters < 1) return MF_ERR_ARG;
   MF_CUDA(pb, cudaSetDevice(pb->device));
   SolverState s0;
@@ -788,6 +802,79 @@ mf_status mf_autotune(mf_problem* pb, int reps, int force_iters, mf_tuning* out)
     out->ms_per_rhs_default = dflt;
   }
   return r;
+}
+
+// ---- checkpoints: everything a continuation reads, in one caller-owned blob ----
+namespace {
+constexpr unsigned long long CKPT_MAGIC = 0x314b43504f46464dull;   // "MFFOPCK1"
+struct CkptHeader {
+  unsigned long long magic, bytes;
+  int dim, nx, ny, nz, precision, rows_per_item, zs_per_item, grid;
+};
+// (device pointer, bytes) of every saved region, in blob order after the header
+std::vector<std::pair<void*, size_t>> ckpt_regions(const mf_problem* pb) {
+  const Desc& d = pb->d;
+  const size_t ts = d.precision ? 4 : 8;
+  const size_t ncomp = d.dim == 2 ? 1 : 3;
+  const size_t nstate = (size_t)d.ncell * ncomp;
+  std::vector<std::pair<void*, size_t>> r;
+  r.push_back({(void*)d.st, sizeof(SolverState)});
+  for (int i = 0; i < 6; ++i) r.push_back({(void*)d.fbuf[i], nstate * 8});
+  r.push_back({d.hd, ncomp * (size_t)d.ncell * ts});
+  if (d.dim == 2) r.push_back({d.hd2, (size_t)d.ncell * ts});
+  r.push_back({(void*)d.log, (size_t)d.log_cap * sizeof(StepLog)});
+  return r;
+}
+size_t ckpt_bytes(const mf_problem* pb) {
+  size_t b = sizeof(CkptHeader);
+  for (const auto& x : ckpt_regions(pb)) b += x.second;
+  return b;
+}
+}  // namespace
+
+size_t mf_checkpoint_bytes(const mf_problem* pb) { return pb ? ckpt_bytes(pb) : 0; }
+
+mf_status mf_checkpoint_save(mf_problem* pb, void* dst) {
+  Range range_("mf_checkpoint_save");
+  if (!pb || !dst) return MF_ERR_ARG;
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  CkptHeader h{CKPT_MAGIC, ckpt_bytes(pb), pb->d.dim, pb->d.nx, pb->d.ny, pb->d.nz, pb->d.precision,
+               pb->d.rows_per_item, pb->d.zs_per_item, pb->d.grid};
+  char* o = (char*)dst;
+  MF_CUDA(pb, cudaMemcpyAsync(o, &h, sizeof(h), cudaMemcpyDefault, pb->stream));
+  o += sizeof(h);
+  for (const auto& x : ckpt_regions(pb)) {
+    MF_CUDA(pb, cudaMemcpyAsync(o, x.first, x.second, cudaMemcpyDefault, pb->stream));
+    o += x.second;
+  }
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));   // the header is a host local
+  return MF_OK;
+}
+
+mf_status mf_checkpoint_restore(mf_problem* pb, const void* src) {
+  Range range_("mf_checkpoint_restore");
+  if (!pb || !src) return MF_ERR_ARG;
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  CkptHeader h;
+  MF_CUDA(pb, cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  if (h.magic != CKPT_MAGIC || h.bytes != ckpt_bytes(pb) || h.dim != pb->d.dim || h.nx != pb->d.nx ||
+      h.ny != pb->d.ny || h.nz != pb->d.nz || h.precision != pb->d.precision) {
+    pb->err = "checkpoint does not match this problem (grid, dimension or precision)";
+    return MF_ERR_ARG;
+  }
+  const char* i = (const char*)src + sizeof(h);
+  for (const auto& x : ckpt_regions(pb)) {
+    MF_CUDA(pb, cudaMemcpyAsync(x.first, i, x.second, cudaMemcpyDefault, pb->stream));
+    i += x.second;
+  }
+  // the work-item shape (it sets the order of the sums) and launch width it was saved with
+  pb->d.rows_per_item = h.rows_per_item;
+  pb->d.zs_per_item = h.zs_per_item;
+  pb->d.grid = h.grid;
+  MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.dev, &pb->d, sizeof(Desc), cudaMemcpyHostToDevice, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  return MF_OK;
 }
 
 mf_status mf_get_info(mf_problem* pb, mf_info* out) {

@@ -27,7 +27,8 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_reset_warm", "mf_set_state", "mf_get_state", "mf_advance", "mf_step",
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
            "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
-           "mf_autotune", "mf_batch_plan"]
+           "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
+           "mf_checkpoint_restore"]
 
 
 class mf_params(ctypes.Structure):
@@ -101,6 +102,9 @@ def load() -> ctypes.CDLL:
         "mf_get_info": (ctypes.c_int, [vp, P(mf_info)]),
         "mf_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, P(mf_tuning)]),
         "mf_batch_plan": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ctypes.c_int, ip, ip, ip]),
+        "mf_checkpoint_bytes": (ctypes.c_size_t, [vp]),
+        "mf_checkpoint_save": (ctypes.c_int, [vp, vp]),
+        "mf_checkpoint_restore": (ctypes.c_int, [vp, vp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -259,6 +263,21 @@ class Problem:
         tu = mf_tuning()
         self._check(self.lib.mf_autotune(self.h, reps, force_iters, ctypes.byref(tu)))
         return {name: getattr(tu, name) for name, _ in mf_tuning._fields_}
+
+    def mf_checkpoint_save(self, out=None):
+        """Save a checkpoint into `out` (a uint8 tensor of mf_checkpoint_bytes, device or host;
+        allocated on the problem's device if None) and return it."""
+        import torch
+        n = self.lib.mf_checkpoint_bytes(self.h)
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=self.device)
+        if out.numel() * out.element_size() < n:
+            raise ValueError(f"checkpoint needs {n} bytes")
+        self._check(self.lib.mf_checkpoint_save(self.h, _dptr(out)))
+        return out
+
+    def mf_checkpoint_restore(self, blob):
+        self._check(self.lib.mf_checkpoint_restore(self.h, _dptr(blob)))
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()
