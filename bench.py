@@ -160,9 +160,11 @@ def cpu_sample(wl, iters: int, budget_s: float):
 
 
 def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128):
-    """Secondary line: the 3D cube (n_grid/2 cells per side in n_grid^3), FP32 transforms."""
+    """Secondary line: the 3D cube (n_grid/2 cells per side in n_grid^3), FP32 transforms,
+    after mf_autotune has picked the work-item shape and launch width (reported beside it)."""
     wl = W.cube_bulk(n_grid, precision=1)
     p = native.from_workload(wl)
+    tune = p.mf_autotune(reps=2, force_iters=2)      # transform work does not depend on the values
     p.mf_set_state(0.0, None, h=1e-3)
     p.mf_advance(1.0, max_attempts=warmup)
     torch.cuda.synchronize()
@@ -182,7 +184,8 @@ def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 12
             "mean_outside_iterations": n_it / max(n_rhs, 1),
             "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
-                         "bytes_model": f"(60 + 60 I) M3 per RHS, M3 = {n_grid}^3 x 4 B"}}
+                         "bytes_model": f"(60 + 60 I) M3 per RHS, M3 = {n_grid}^3 x 4 B"},
+            "autotune": tune}
 
 
 def autotune_leg(native, W, torch, n_grid: int):
