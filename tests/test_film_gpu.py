@@ -130,6 +130,36 @@ def test_rhs_full_size_rect_film_2048_fp32():
     _rhs_pair(wl, g, [0.05], force=3, precision_tol=TOL32)
 
 
+@pytest.mark.slow
+def test_step_full_size_rect_film_2048_fp32_as_benchmarked():
+    """The benchmark's launch: the 2048^2 film from the bench's start state, one persistent
+    mf_advance launch of one BS23 attempt (4 right-hand sides with converged outside
+    iterations).  The FP64 oracle replays it with the GPU's step size and per-stage iteration
+    counts; the state increment and the h_z increment agree within the precision form's 2e-4."""
+    wl = W.rect_film_2048(precision=1)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    p = gpu_of(wl)
+    p.mf_set_state(0.05, dev(g0), h=2e-5)
+    p.mf_advance(1.0, max_attempts=1)
+    log = p.mf_get_log()
+    assert len(log) == 1 and log[0][3] == 1 and min(log[0][4]) >= 1
+    g = torch.zeros((2048, 2048), dtype=torch.float64, device="cuda")
+    t1, _ = p.mf_get_state(g)
+    # the oracle runs the logged iteration counts; a stop-test tolerance it always meets keeps
+    # its status (and so its warm start) that of the converged GPU stages
+    o = oracle_of(wl, iter_tol=1.0)
+    s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept, on_attempt=o.begin_attempt)
+    s.start(0.05, g0, 1.0)
+    s.replay([LogEntry(*e) for e in log])
+    assert s.t == t1
+    dg_gpu = g.cpu().numpy() - g0
+    dg_ref = s.y - g0
+    assert rel_l2(dg_gpu, dg_ref) < TOL32
+    dhz = o.hz(t1, s.y) - o.hz(0.05, g0)
+    dhz_gpu = o.hz(t1, g.cpu().numpy()) - o.hz(0.05, g0)
+    assert rel_l2(dhz_gpu, dhz) < TOL32
+
+
 def _replay(o, wl, log, y0):
     s = BS23(o.rhs, o.wf, rtol=wl.rtol, atol=wl.atol, on_accept=o.accept, on_attempt=o.begin_attempt)
     s.start(wl.t0, y0, wl.t1)
