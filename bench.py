@@ -391,24 +391,21 @@ def main():
     # the integrator may stop early only at t = 1 (end of the cycle)
     t_now, _ = p.mf_get_state()
 
-    # end-to-end through the public API with host buffers: H2D state, one step, D2H state + m_z
-    host = torch.empty((wl.ny, wl.nx), dtype=torch.float64).pin_memory()
-    dev_y = torch.empty((wl.ny, wl.nx), dtype=torch.float64, device="cuda")
-    p.mf_get_state(dev_y)
-    host.copy_(dev_y)
-    torch.cuda.synchronize()
+    # end-to-end through the public API with the solver state resident in pinned host memory:
+    # every step restores the checkpoint (state, first-same-as-last derivative, warm start, step
+    # size, counters) from the host, advances one step, saves it back and reads m_z, so the
+    # steps follow the timed region's trajectory and do the same work
+    nblob = native.load().mf_checkpoint_bytes(p.h)
+    blob = torch.empty(nblob, dtype=torch.uint8).pin_memory()
+    p.mf_checkpoint_save(blob)
     e2e_steps = max(3, args.steps // 2)
     re0, ie0, _ = counters()
-    t_e, h_e = p.mf_get_state()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     for _ in range(e2e_steps):
-        # the same trajectory as the timed region: state and step size carried over each step
-        dev_y.copy_(host, non_blocking=True)
-        p.mf_set_state(t_e, dev_y, h=h_e)
+        p.mf_checkpoint_restore(blob)
         p.mf_advance(1.0, max_attempts=1)
-        t_e, h_e = p.mf_get_state(dev_y)
-        host.copy_(dev_y, non_blocking=True)
+        p.mf_checkpoint_save(blob)
         m = p.mf_readout(native.MF_READ_MOMENT)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
@@ -456,12 +453,11 @@ def main():
                          "kernel": "film_kernel<float> (persistent)",
                          "bytes_model": "(19 + 14 I) M per RHS, M = 2048^2 x 4 B"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": ncell * 8,
-                    "d2h_bytes_per_step": ncell * 8 + 8, "ms_per_step": 1000.0 * e2e_s / e2e_steps,
-                    "note": "each step sets the state from host memory, which discards the "
-                            "first-same-as-last derivative: k1 is evaluated again (4 right-hand "
-                            "sides per step instead of 3; the extra one starts from its own "
-                            "converged iterate and needs few outside iterations)"},
+            "e2e": {"value": e2e_all, "unit": UNIT, "h2d_bytes_per_step": nblob,
+                    "d2h_bytes_per_step": nblob + 8, "ms_per_step": 1000.0 * e2e_s / e2e_steps,
+                    "note": "solver state in pinned host memory: each step restores the whole "
+                            "checkpoint (state, derivative buffers, warm start, step log) from "
+                            "the host, advances one step and saves it back, then reads m_z"},
             "gpu_launches": 1,
             "clocks": ck.summary(),
             "bulk": bulk,
