@@ -206,7 +206,8 @@ def autotune_leg(native, W, torch, n_grid: int):
             "timing": "CUDA events, 5 launches of one right-hand side with 4 forced outside iterations"}
 
 
-def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 2):
+def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 2,
+              max_side: int = 512):
     """Secondary line: a sweep of `count` independent films (seeded shapes, sides 64..512 cells,
     grids twice the film, n in {19, 30, 50}, ramp amplitudes in [0.2, 1]), FP32 transforms,
     advanced by one mf_advance_batch call (films smaller than the GPU in shared persistent
@@ -214,7 +215,7 @@ def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 
     in the same states advanced one after the other (one launch each): the two do the same
     work (a batched film's result is bit-identical to its own launch's).  Value = right-hand
     sides of all films per second."""
-    wls = W.film_batch(count, seed=3, max_side=512, precision=1)
+    wls = W.film_batch(count, seed=3, max_side=max_side, precision=1)
     sets = []
     for _ in range(2):
         ps = [native.from_workload(wl) for wl in wls]
@@ -233,20 +234,25 @@ def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 
         i1 = [p.mf_get_info() for p in ps]
         n_rhs = sum(b["n_rhs"] - a["n_rhs"] for a, b in zip(i0, i1))
         n_it = sum(b["n_iters"] - a["n_iters"] for a, b in zip(i0, i1))
-        return n_rhs, n_it, sec
+        # (19 + 14 I) M per right-hand side, M = one FP32 field of the film's grid
+        alg = sum(rhs_bytes(b["n_rhs"] - a["n_rhs"], b["n_iters"] - a["n_iters"], wl.nx * wl.ny * 4.0)
+                  for a, b, wl in zip(i0, i1, wls))
+        return n_rhs, n_it, sec, alg
 
     ps, qs = sets
-    n_rhs, n_it, sec = timed(ps, lambda: native.advance_batch(ps, [1.0] * count, max_attempts=steps))
+    n_rhs, n_it, sec, alg = timed(ps, lambda: native.advance_batch(ps, [1.0] * count, max_attempts=steps))
 
     def one_by_one():
         for q in qs:
             q.mf_advance(1.0, max_attempts=steps)
 
-    s_rhs, _, s_sec = timed(qs, one_by_one)
+    s_rhs, _, s_sec, _ = timed(qs, one_by_one)
     cells = sum(wl.nx * wl.ny for wl in wls)
-    return {"workload": f"film_batch_seed3_{count}", "value": n_rhs / sec, "unit": UNIT,
+    name = f"film_batch_seed3_{count}" + ("" if max_side == 512 else f"_max{max_side}")
+    return {"workload": name, "value": n_rhs / sec, "unit": UNIT,
             "films": count, "grid_cells": cells, "steps_per_film": steps,
             "mean_outside_iterations": n_it / max(n_rhs, 1),
+            "algorithmic_bytes": alg, "achieved_gbs": alg / sec / 1e9,
             "one_launch_per_film": {"value": s_rhs / s_sec, "unit": UNIT, "same_work": s_rhs == n_rhs,
                                     "note": "a copy of the same films in the same states, advanced one after the other"},
             "speedup": (n_rhs / sec) / (s_rhs / s_sec),
@@ -330,6 +336,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the bulk and full-ramp legs")
     ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
+    ap.add_argument("--only", choices=["batch"], help="run one secondary leg alone (profiling)")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-max-side", type=int, default=512)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -348,6 +357,11 @@ def main():
     from paper_1801_04869_gb300 import native
 
     torch.cuda.set_device(local)
+    if args.only == "batch":
+        if rank == 0:
+            print(json.dumps(batch_leg(native, W, torch, count=args.batch_count,
+                                       max_side=args.batch_max_side)))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -158,16 +158,20 @@ mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_target
 
 /* The arrangement mf_advance_batch uses for n films of one device and precision (host only, no
    GPU work): nx, ny are the films' grids, own_grid[i] the CTAs of film i's own launch
-   (mf_info.grid), coresident the CTAs that fit the GPU at once.  Films are ordered by
-   transform work (cells x log2 cells), largest first, into order[0..n-1].  A film with
-   own_grid >= coresident gets launch[i] = -1 (a launch of its own, ctas[i] = coresident).
-   The others fill shared launches 0, 1, ... in that order, at most 256 films each, a launch
-   being closed before a film whose share of the grid in proportion to its work would be
-   below one CTA; ctas[i] is film i's CTA count in its launch (1 <= ctas[i] <= own_grid[i],
-   and a launch's CTAs sum to at most coresident), its range following the launch's earlier
-   films in `order`.  Returns the number of shared launches, or -1 for invalid arguments. */
-int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid, int coresident,
-                  int* order, int* launch, int* ctas);
+   (mf_info.grid), work[i] > 0 its expected work (NULL: cells x log2 cells), coresident the CTAs
+   that fit the GPU at once.  mf_advance_batch passes cells x log2 cells times the film's field
+   passes per step attempt (19 per right-hand side, 14 per outside iteration) measured in its
+   previous batch call, else averaged over its history.  Films are ordered by work, most first,
+   into order[0..n-1].  A film with own_grid >= coresident gets launch[i] = -1 (a launch of its
+   own, ctas[i] = coresident).  The others fill shared launches 0, 1, ... in that order, at
+   most 256 films each, a launch being closed before a film whose share of the grid in
+   proportion to its work would be below one CTA; ctas[i] is film i's CTA count in its launch
+   (1 <= ctas[i] <= own_grid[i], a launch's CTAs sum to at most coresident, and the largest
+   work per CTA of a launch is as small as whole CTAs allow), its range following the launch's
+   earlier films in `order`.  Returns the number of shared launches, or -1 for invalid
+   arguments. */
+int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid, const double* work,
+                  int coresident, int* order, int* launch, int* ctas);
 
 /* One BS23 step attempt towards t_max; *accepted (may be NULL) is 1 if it was accepted. */
 mf_status mf_step(mf_problem* pb, double t_max, int* accepted);

@@ -29,6 +29,7 @@ struct mf_problem {
   double* scratch_m;            // device scalar(s) for moment readouts (in the workspace)
   std::string err;
   bool have_knots;
+  double batch_work = 0.0;      // field passes per step attempt in the last mf_advance_batch
 };
 
 namespace {
@@ -456,21 +457,26 @@ static double film_cost(int nx, int ny) {
 // CTAs per film of a shared launch: one each, then one at a time to the film with the most
 // work per CTA until the grid is full or every film has the CTAs its own launch would use
 // (this minimises the largest work per CTA, which sets how long the launch lasts)
-static void split_ctas(const int* nx, const int* ny, const int* own, const int* films, int n,
-                       int total, int* ctas) {
+static void split_ctas(const double* cost, const int* own, const int* films, int n, int total,
+                       int* ctas) {
   std::priority_queue<std::pair<double, int>> q;
   for (int k = 0; k < n; ++k) {
     const int i = films[k];
     ctas[i] = 1;
-    if (ctas[i] < own[i]) q.push({film_cost(nx[i], ny[i]), k});
+    if (ctas[i] < own[i]) q.push({cost[i], k});
   }
   for (int used = n; used < total && !q.empty(); ++used) {
-    const int i = films[q.top().second];
     const int k = q.top().second;
+    const int i = films[k];
     q.pop();
     ++ctas[i];
-    if (ctas[i] < own[i]) q.push({film_cost(nx[i], ny[i]) / ctas[i], k});
+    if (ctas[i] < own[i]) q.push({cost[i] / ctas[i], k});
   }
+}
+
+// field passes (19 per right-hand side, 14 per outside iteration) per step attempt
+static double passes_per_attempt(long long rhs, long long iters, long long attempts) {
+  return (19.0 * (double)rhs + 14.0 * (double)iters) / (double)std::max(attempts, 1LL);
 }
 
 // Advance the films pbs[idx[k]] (one device, one precision) as mf_batch_plan arranges them;
@@ -504,11 +510,23 @@ static void advance_films_together(mf_problem* const* pbs, const std::vector<int
   }
   const int n = (int)live.size();
   if (n == 0) return;
+  // each film's work per attempt: what it took in the previous batch call, else its average
+  // so far, else 3.5 right-hand sides of 5 outside iterations; times cells x log2 cells
   std::vector<int> nx(n), ny(n), own(n), order(n), launch(n), ctas(n);
+  std::vector<double> work(n);
+  std::vector<SolverState> before(n);
   for (int k = 0; k < n; ++k) {
-    nx[k] = pbs[live[k]]->d.nx; ny[k] = pbs[live[k]]->d.ny; own[k] = pbs[live[k]]->d.grid;
+    mf_problem* f = pbs[live[k]];
+    nx[k] = f->d.nx; ny[k] = f->d.ny; own[k] = f->d.grid;
+    if (read_state(f, &before[k]) != MF_OK) std::memset(&before[k], 0, sizeof(SolverState));
+    const SolverState& b0 = before[k];
+    double w = f->batch_work;
+    if (!(w > 0.0)) w = b0.n_attempts > 0 ? passes_per_attempt(b0.n_rhs, b0.n_iters, b0.n_attempts)
+                                          : passes_per_attempt(7, 35, 2);
+    const double c = (double)nx[k] * (double)ny[k];
+    work[k] = w * c * std::log2(c);
   }
-  const int nlaunch = mf_batch_plan(n, nx.data(), ny.data(), own.data(), per_sm * nsm,
+  const int nlaunch = mf_batch_plan(n, nx.data(), ny.data(), own.data(), work.data(), per_sm * nsm,
                                     order.data(), launch.data(), ctas.data());
   std::vector<int> alone, shared;
   for (int k : order) {
@@ -545,19 +563,30 @@ static void advance_films_together(mf_problem* const* pbs, const std::vector<int
   e = shared.empty() ? cudaSuccess : cudaStreamSynchronize(s);
   for (int i : shared) st[i] = e == cudaSuccess ? launch_finish(pbs[i]) : cuda_fail(pbs[i], e, "shared persistent launch");
   for (int i : alone) st[i] = launch_finish(pbs[i]);
+  // remember what each film's attempts cost in this call for the next arrangement
+  for (int k = 0; k < n; ++k) {
+    SolverState a1;
+    mf_problem* f = pbs[live[k]];
+    if (read_state(f, &a1) != MF_OK) continue;
+    const long long att = a1.n_attempts - before[k].n_attempts;
+    if (att > 0)
+      f->batch_work = passes_per_attempt(a1.n_rhs - before[k].n_rhs, a1.n_iters - before[k].n_iters, att);
+  }
 }
 
-int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid,
-                             int coresident, int* order, int* launch, int* ctas) {
+int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid, const double* work,
+                  int coresident, int* order, int* launch, int* ctas) {
   if (n < 0 || (n > 0 && (!nx || !ny || !own_grid || !order || !launch || !ctas)) || coresident < 1)
     return -1;
-  for (int i = 0; i < n; ++i)
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
     if (nx[i] < 1 || ny[i] < 1 || own_grid[i] < 1) return -1;
+    cost[i] = work ? work[i] : film_cost(nx[i], ny[i]);
+    if (!(cost[i] > 0.0) || !std::isfinite(cost[i])) return -1;
+  }
   for (int i = 0; i < n; ++i) order[i] = i;
-  // largest first (stable: equal films keep their order)
-  std::stable_sort(order, order + n, [&](int a, int b) {
-    return film_cost(nx[a], ny[a]) > film_cost(nx[b], ny[b]);
-  });
+  // most work first (stable: equal films keep their order)
+  std::stable_sort(order, order + n, [&](int a, int b) { return cost[a] > cost[b]; });
   // films whose own launch fills the GPU keep it
   std::vector<int> sh;
   for (int k = 0; k < n; ++k) {
@@ -565,20 +594,20 @@ int mf_batch_plan(int n, const int* nx, const int* ny, const int* own_grid,
     if (own_grid[i] >= coresident) { launch[i] = -1; ctas[i] = coresident; }
     else sh.push_back(i);
   }
-  // the others fill shared launches, largest first; a launch is closed before a film whose
+  // the others fill shared launches, most work first; a launch is closed before a film whose
   // share of the grid in proportion to its work would be below one CTA
   const size_t cap = (size_t)std::min(MAX_BATCH, coresident);
   int nl = 0;
   for (size_t k0 = 0; k0 < sh.size(); ++nl) {
-    double sum = film_cost(nx[sh[k0]], ny[sh[k0]]);
+    double sum = cost[sh[k0]];
     size_t k1 = k0 + 1;
     for (; k1 < sh.size() && k1 - k0 < cap; ++k1) {
-      const double c = film_cost(nx[sh[k1]], ny[sh[k1]]);
+      const double c = cost[sh[k1]];
       if (sum + c > (double)coresident * c) break;
       sum += c;
     }
     for (size_t k = k0; k < k1; ++k) launch[sh[k]] = nl;
-    split_ctas(nx, ny, own_grid, sh.data() + k0, (int)(k1 - k0), coresident, ctas);
+    split_ctas(cost.data(), own_grid, sh.data() + k0, (int)(k1 - k0), coresident, ctas);
     k0 = k1;
   }
   return nl;

@@ -101,7 +101,7 @@ def load() -> ctypes.CDLL:
         "mf_readout_of": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, vp, vp]),
         "mf_get_info": (ctypes.c_int, [vp, P(mf_info)]),
         "mf_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, P(mf_tuning)]),
-        "mf_batch_plan": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ctypes.c_int, ip, ip, ip]),
+        "mf_batch_plan": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, dp, ctypes.c_int, ip, ip, ip]),
         "mf_checkpoint_bytes": (ctypes.c_size_t, [vp]),
         "mf_checkpoint_save": (ctypes.c_int, [vp, vp]),
         "mf_checkpoint_restore": (ctypes.c_int, [vp, vp]),
@@ -314,13 +314,14 @@ def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int 
     return st, it.value, msg.value.decode()
 
 
-def batch_plan(nx, ny, own_grid, coresident: int):
+def batch_plan(nx, ny, own_grid, coresident: int, work=None):
     """mf_batch_plan (host only): (number of shared launches, order, launch, ctas)."""
     lib = load()
     n = len(nx)
     arr = lambda v: (ctypes.c_int * max(n, 1))(*[int(x) for x in v])
     order, launch, ctas = arr([0] * n), arr([0] * n), arr([0] * n)
-    r = lib.mf_batch_plan(n, arr(nx), arr(ny), arr(own_grid), int(coresident), order, launch, ctas)
+    w = None if work is None else (ctypes.c_double * max(n, 1))(*[float(x) for x in work])
+    r = lib.mf_batch_plan(n, arr(nx), arr(ny), arr(own_grid), w, int(coresident), order, launch, ctas)
     if r < 0:
         raise ValueError("mf_batch_plan: invalid arguments")
     return r, list(order)[:n], list(launch)[:n], list(ctas)[:n]

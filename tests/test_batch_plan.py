@@ -2,6 +2,8 @@
 import math
 import os
 
+import numpy as np
+
 import pytest
 
 import workloads as W
@@ -28,10 +30,11 @@ def own_grid(g):
     return min(CORESIDENT, g[0] // 2 + 1)
 
 
-def check(films, own, nl, order, launch, ctas, coresident=CORESIDENT):
+def check(films, own, nl, order, launch, ctas, coresident=CORESIDENT, work=None):
     n = len(films)
+    w = work if work is not None else [cost(f) for f in films]
     assert sorted(order) == list(range(n))
-    costs = [cost(films[i]) for i in order]
+    costs = [w[i] for i in order]
     assert all(a >= b for a, b in zip(costs, costs[1:]))
     shared = [i for i in order if launch[i] >= 0]
     assert [launch[i] for i in shared] == sorted(launch[i] for i in shared)
@@ -45,23 +48,23 @@ def check(films, own, nl, order, launch, ctas, coresident=CORESIDENT):
         m = [i for i in shared if launch[i] == j]
         assert 1 <= len(m) <= min(256, coresident)
         assert sum(ctas[i] for i in m) <= coresident
-        c = [cost(films[i]) for i in m]
+        c = [w[i] for i in m]
         # every film's share of the grid in proportion to its work is at least one CTA
         assert sum(c) <= coresident * min(c) * (1 + 1e-12)
         # the next launch's first film would have broken that (unless the 256-film cap closed it)
         nxt = [i for i in shared if launch[i] == j + 1]
         if nxt and len(m) < min(256, coresident):
-            cn = cost(films[nxt[0]])
+            cn = w[nxt[0]]
             assert sum(c) + cn > coresident * cn
         # no CTA can move between two films of the launch and lower its largest work per CTA
         # (with the grid full or every film at its own launch width)
-        worst = max(m, key=lambda i: cost(films[i]) / ctas[i])
-        wr = cost(films[worst]) / ctas[worst]
+        worst = max(m, key=lambda i: w[i] / ctas[i])
+        wr = w[worst] / ctas[worst]
         if ctas[worst] < own[worst]:
             assert sum(ctas[i] for i in m) == coresident
             for a in m:
                 if a != worst and ctas[a] > 1:
-                    assert cost(films[a]) / (ctas[a] - 1) >= wr * (1 - 1e-12)
+                    assert w[a] / (ctas[a] - 1) >= wr * (1 - 1e-12)
 
 
 def test_sweep_of_256_films(plan):
@@ -100,3 +103,19 @@ def test_edge_cases(plan):
         plan([128], [128], [0], CORESIDENT)
     with pytest.raises(ValueError):
         plan([128], [128], [65], 0)
+
+
+def test_measured_work_weights(plan):
+    """Equal grids, unequal measured work: the film that needed the most outside iterations
+    gets the most CTAs, and the largest work per CTA is as small as whole CTAs allow."""
+    films = [(256, 256)] * 40
+    own = [own_grid(f) for f in films]
+    r = np.random.default_rng(5)
+    work = [cost(f) * (19 * 3.5 + 14 * 3.5 * it) for f, it in zip(films, r.uniform(2, 40, 40))]
+    nl, order, launch, ctas = plan([256] * 40, [256] * 40, own, CORESIDENT, work=work)
+    check(films, own, nl, order, launch, ctas, work=work)
+    assert nl == 1 and sum(ctas) == CORESIDENT
+    heavy = max(range(40), key=lambda i: work[i])
+    assert ctas[heavy] == max(ctas) and order[0] == heavy
+    with pytest.raises(ValueError):
+        plan([128], [128], [65], CORESIDENT, work=[0.0])
