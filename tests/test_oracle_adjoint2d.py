@@ -1,0 +1,95 @@
+"""Pins of the film-solve adjoint oracle: consistency with the forward oracle, the dot-product
+test of the transposed outside iteration, and central finite differences of the map."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.adjoint2d import FilmAdjoint
+from oracle.film2d import FilmProblem
+from oracle.waveform import Waveform
+
+N, L = 32, 2.0
+KT, KV = [0.0, 0.5, 1.0], [0.0, 0.3, 0.45]
+
+
+def _setup(n_power=19.0, iters=4, seed=31, amplitude=1.6):
+    # amplitude 1.6 on this grid puts |j| just below jc (the smoothing rounds the critical-state
+    # slope), where the power law is sensitive to jc
+    mask = W.film_mask(N, N, L, L, "rect", ax=1.0, ay=0.75)
+    jc = W.jc_map_lognormal((N, N), seed=seed, sigma=0.05)
+    p = FilmProblem(N, N, L, L, mask, n=n_power, rho_out=1.0, waveform=Waveform(KT, KV), jc=jc,
+                    iter_tol=0.0, iter_max=iters)
+    g0 = W.film_state(mask, L, L, seed=seed, amplitude=amplitude)
+    return p, FilmAdjoint(p, iters), g0, np.array(p.jc)
+
+
+def test_forward_rhs_equals_the_film_oracle():
+    """Cold start and a fixed iteration count: the adjoint's f is FilmProblem.rhs."""
+    p, a, g0, jc = _setup()
+    s = p.wf.hedot(0.2)
+    ref, it, _ = p.rhs(0.2, g0, None, a.I)
+    got, _ = a.rhs(g0, jc, s)
+    assert it == a.I
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_transposed_outside_iteration_dot_product():
+    p, a, _, _ = _setup(iters=5)
+    r = W.rng(32)
+    hin = np.where(p.conductor, r.standard_normal((N, N)), 0.0)
+    s = 0.37
+    v = r.standard_normal((N, N))
+    hb, sb = a.P_T(v)
+    lhs = float((a.P(hin, s) * v).sum())
+    rhs = float((hin * hb).sum()) + s * sb
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
+
+
+def _fd(fun, x, d, eps):
+    return (fun(x + eps * d) - fun(x - eps * d)) / (2 * eps)
+
+
+def test_rhs_vjp_matches_finite_differences():
+    p, a, g0, jc = _setup()
+    r = W.rng(33)
+    s = 0.3
+    v = r.standard_normal((N, N))
+    _, tape = a.rhs(g0, jc, s)
+    gb, cb, sb = a.rhs_vjp(tape, jc, v)
+    dg = np.where(p.conductor, r.standard_normal((N, N)), 0.0)
+    dc = np.where(p.sc, r.standard_normal((N, N)), 0.0)
+    fg = _fd(lambda x: float((a.rhs(x, jc, s)[0] * v).sum()), g0, dg, 1e-6)
+    fc = _fd(lambda x: float((a.rhs(g0, x, s)[0] * v).sum()), jc, dc, 1e-6)
+    fs = _fd(lambda x: float((a.rhs(g0, jc, x)[0] * v).sum()), s, 1.0, 1e-6)
+    assert abs(fg - (gb * dg).sum()) < 1e-6 * abs(fg)
+    assert abs(fc - (cb * dc).sum()) < 1e-6 * abs(fc)
+    assert abs(fs - sb) < 1e-6 * abs(fs)
+
+
+@pytest.mark.parametrize("n_power", [1.0, 19.0])
+def test_solve_gradient_matches_finite_differences(n_power):
+    """dL/djc and dL/dv of the frozen-step solve against central differences of L, for the
+    Ohmic sheet (rho = 1/jc) and a power-law film in a near-critical state."""
+    p, a, g0, jc = _setup(n_power=n_power)
+    steps = [(0.1 + 0.002 * i, 0.002) for i in range(6)]
+    target = W.rng(34).standard_normal((N, N)) * 0.01
+    Lv, cb, vb = a.gradient(g0, jc, KT, KV, steps, target)
+    assert Lv == pytest.approx(a.loss(g0, jc, KT, KV, steps, target), rel=1e-14)
+    kv = np.array(KV)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        fd = _fd(lambda x: a.loss(g0, jc, KT, x, steps, target), kv, e, 1e-5)
+        assert abs(fd - vb[k]) <= 1e-6 * max(abs(fd), 1e-12) + 1e-14, (k, fd, vb[k])
+    # the most sensitive cell and cells across the film (edge, core, corner)
+    film = np.argwhere(p.sc)
+    picks = [np.unravel_index(np.argmax(np.abs(cb)), cb.shape)]
+    picks += [tuple(film[i]) for i in (0, len(film) // 3, len(film) // 2, -1)]
+    scale = np.abs(cb).max()
+    assert scale > 1e-4
+    for iy, ix in picks:
+        e = np.zeros((N, N))
+        e[iy, ix] = 1.0
+        fd = _fd(lambda x: a.loss(g0, x, KT, KV, steps, target), jc, e, 1e-5)
+        assert abs(fd - cb[iy, ix]) <= 1e-6 * abs(fd) + 1e-8 * scale, (iy, ix, fd, cb[iy, ix])
+    assert np.all(cb[~p.sc] == 0.0)
