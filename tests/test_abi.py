@@ -58,3 +58,21 @@ def test_workspace_query_and_argument_checks(lib):
     h = ctypes.c_void_p()
     p.nx = 128
     assert lib.mf_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == native.MF_ERR_WORKSPACE
+
+
+def test_null_and_invalid_arguments_are_refused_without_a_gpu(lib):
+    """The documented argument checks run before any CUDA call."""
+    import ctypes
+    from paper_1801_04869_gb300 import native
+    assert lib.mf_autotune(None, 1, 1, None) == native.MF_ERR_ARG
+    assert lib.mf_checkpoint_bytes(None) == 0
+    assert lib.mf_checkpoint_save(None, None) == native.MF_ERR_ARG
+    assert lib.mf_checkpoint_restore(None, None) == native.MF_ERR_ARG
+    assert lib.mf_advance_batch(None, 1, None, 1, None) == native.MF_ERR_ARG
+    assert lib.mf_advance(None, 1.0, 1) == native.MF_ERR_ARG
+    assert lib.mf_rhs(None, 0.0, None, None, None) == native.MF_ERR_ARG
+    assert lib.mf_get_info(None, None) == native.MF_ERR_ARG
+    one = (ctypes.c_int * 1)(64)
+    out = (ctypes.c_int * 1)()
+    assert lib.mf_batch_plan(-1, one, one, one, None, 304, out, out, out) == -1
+    assert lib.mf_batch_plan(0, None, None, None, None, 304, None, None, None) == 0
