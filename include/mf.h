@@ -196,6 +196,17 @@ mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, d
 /* Counters, state and launch configuration. */
 mf_status mf_get_info(mf_problem* pb, mf_info* out);
 
+/* Transpose of a film's outside iteration (Eqs. 10-12), the linear core of the right-hand
+   side's vector-Jacobian product: with a cold start (free-space h_dot = h_e_dot) and exactly
+   `iters` iterations the iteration maps (h_dot_in, h_e_dot) linearly to g_dot; given the
+   cotangent d_v of g_dot (device FP64, nx*ny), this writes the cotangent of h_dot_in to
+   d_hin_bar (device FP64, nx*ny, zero on free space) and that of h_e_dot to *sbar (host, may be
+   NULL).  One persistent launch on the problem's stream; waits for it.  Uses the warm start's
+   buffers and clears the warm start.  MF_ERR_ARG for a bulk problem or a film without free
+   space.  The adjoint has no counterpart in the paper. */
+mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
+                              double* sbar);
+
 /* Checkpoints: everything a continuation reads — the integrator state and counters, the six
    FP64 state/derivative buffers (with the first-same-as-last derivative), the outside
    iteration's warm start, the step log, and the work-item shape and launch width.  Restoring a

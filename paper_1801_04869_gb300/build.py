@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libmf.so")
-SOURCES = ["mf_film.cu", "mf_film_batch.cu", "mf_bulk.cu", "mf_api.cu", "mf_noalloc.cu"]
+SOURCES = ["mf_film.cu", "mf_film_batch.cu", "mf_film_adjoint.cu", "mf_bulk.cu", "mf_api.cu",
+           "mf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -32,6 +32,12 @@ struct mf_problem {
   double batch_work = 0.0;      // field passes per step attempt in the last mf_advance_batch
 };
 
+namespace mf {
+// transposed outside iteration of a film (csrc/mf_film_adjoint.cu)
+cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
+                                double* sbar, int iters, cudaStream_t s);
+}  // namespace mf
+
 namespace {
 
 // NVTX range over one host call (shown by nsys / ncu timelines; free when no tool is attached)
@@ -904,6 +910,27 @@ mf_status mf_checkpoint_restore(mf_problem* pb, const void* src) {
   MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.dev, &pb->d, sizeof(Desc), cudaMemcpyHostToDevice, pb->stream));
   MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
   return MF_OK;
+}
+
+mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
+                              double* sbar) {
+  Range range_("mf_film_outside_vjp");
+  if (!pb || !d_v || !d_hin_bar || iters < 1) return MF_ERR_ARG;
+  if (pb->d.dim != 2 || pb->d.nout <= 0) {
+    pb->err = "the transposed outside iteration needs a film with free space";
+    return MF_ERR_ARG;
+  }
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  MF_CUDA(pb, cudaMemsetAsync(pb->d.gb, 0, sizeof(GridBarrier), pb->stream));
+  cudaError_t e = film_adjoint_launch(pb->d.precision, pb->d, d_v, d_hin_bar, pb->scratch_m, iters,
+                                      pb->stream);
+  if (e != cudaSuccess) return cuda_fail(pb, e, "adjoint kernel launch");
+  mf_status r = launch_finish(pb);
+  if (r == MF_OK && sbar) {
+    MF_CUDA(pb, cudaMemcpyAsync(sbar, pb->scratch_m, sizeof(double), cudaMemcpyDeviceToHost, pb->stream));
+    MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  }
+  return r;
 }
 
 mf_status mf_get_info(mf_problem* pb, mf_info* out) {

@@ -1,0 +1,184 @@
+// Transpose of a film's outside iteration (Eqs. 10-12), the linear core of the right-hand
+// side's vector-Jacobian product.  The adjoint has no counterpart in the paper.
+//
+// With a cold start and a fixed count I, the iteration maps (h_dot_in, h_e_dot) linearly to
+// g_dot (the conductor's output):
+//   h_0 = shift(h_dot_in on the conductor, h_e_dot on free space)        shift: Eq. 10
+//   u_i = K1 h_i,  g_i = u_i - C(u_i)                                     Eq. 11 (K1 = 2/|k|)
+//   h_{i+1} = shift(h_i - out K2 (out g_i))                               Eq. 12 (K2 = lambda |k|/2 G)
+//   g_dot = conductor * g_{I-1}
+// Its transpose runs the loop backwards.  K1 and K2 are real and even, so they are their own
+// transposes; the centring (-C) and the shift (-A) are rank-one corrections whose transposes
+// need one grid sum each, applied after the transform through the precomputed responses
+// q1 = K1 out and q2 = K2 out (by linearity), so each backward iteration is two round trips,
+// as forward:
+//   V3  hbar_i = zbar_i + K1 gbar_i - (S_i / n_out) q1      (zbar_{I-1} = 0), tot_i = sum_out hbar_i
+//   V5  gbar_{i-1} = out (K2(-out hbar_i) + (tot_i / n_out) q2),  zbar_{i-1} = hbar_i - tot_i / n_out,
+//       S_{i-1} = sum gbar_{i-1};   sbar += (N / n_out) tot_i
+//   end hbar_in = conductor * (hbar_0 - tot_0 / n_out),  sbar += (N / n_out) tot_0
+// The h_dot buffers of the warm start hold hbar and zbar, so the warm start is cleared.
+#include "mf_film.cuh"
+
+namespace mf {
+
+struct AdjArgs {
+  const double* v;      // cotangent of g_dot (FP64, ncell)
+  double* hin_bar;      // cotangent of h_dot_in (FP64, ncell; 0 on free space)
+  double* sbar;         // cotangent of h_e_dot (FP64 scalar)
+  int iters;
+};
+
+// V1: gbar_{I-1} = conductor * v, and its sum
+template <typename T>
+struct EpiPT0 : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  const double* v;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<double> x = ld4(v + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T g = mask_at(m, q) != 0 ? (T)x.v[q] : (T)0;
+      this->acc += g;
+      out[0].v[q] = g;
+    }
+  }
+};
+
+// V3: hbar = zbar + K1 gbar - (S/n_out) q1 -> hd; sum over free space; forward of -out hbar
+template <typename T>
+struct EpiPTh : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  const T* zbar;        // null on the first backward iteration
+  T s_q1;               // S / n_out
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> q1 = ldg4(P.q1 + i);
+    V4<T> z;
+    if (zbar) z = ld4(zbar + i);
+    V4<T> h;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h.v[q] = (zbar ? z.v[q] : (T)0) + in[0].v[q] - s_q1 * q1.v[q];
+      const bool o = mask_at(m, q) == 0;
+      if (o) this->acc += h.v[q];
+      out[0].v[q] = o ? -h.v[q] : (T)0;
+    }
+    st4(P.hd + i, h);
+  }
+};
+
+// V5: gbar = out (K2(-out hbar) + (tot/n_out) q2), sum; zbar = hbar - tot/n_out -> zbuf
+template <typename T>
+struct EpiPTg : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  T* zbuf;
+  T t_q;                // tot / n_out
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> q2 = ldg4(P.q2 + i);
+    const V4<T> h = ld4(P.hd + i);
+    V4<T> z;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T g = mask_at(m, q) == 0 ? in[0].v[q] + t_q * q2.v[q] : (T)0;
+      this->acc += g;
+      out[0].v[q] = g;
+      z.v[q] = h.v[q] - t_q;
+    }
+    st4(zbuf + i, z);
+  }
+};
+
+// end: hbar_in = conductor * (hbar_0 - tot_0/n_out)
+template <typename T>
+struct EpiPTout : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  double* dst;
+  T t_q;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> h = ld4(P.hd + i);
+    V4<double> r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r.v[q] = mask_at(m, q) != 0 ? (double)(h.v[q] - t_q) : 0.0;
+    st4(dst + i, r);
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restrict__ dg, AdjArgs a) {
+  C2<T>* sm = dsm<T>();
+  __shared__ Shared sh;
+  __shared__ __align__(16) unsigned char objraw[sizeof(Film<T>)];
+  const Desc& d = *dg;
+  SolverState* st = d.st;
+  if (threadIdx.x == 0) {
+    sh.bar_passed = 0;
+    new (objraw) Film<T>(d, sm, sh, (int)blockIdx.x, gridDim.x);
+  }
+  __syncthreads();
+  Film<T>& F = *reinterpret_cast<Film<T>*>(objraw);
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const double nout = (double)d.nout, N = (double)F.ncell;
+  T* const zbuf = (T*)d.hd2;
+  int status = ST_OK;
+  double sbar = 0.0;
+  do {
+    {
+      EpiPT0<T> e; e.P = F.ptrs(); e.v = a.v;
+      F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, 0);                         // V1
+    }
+    if (!F.sync(50)) { status = ST_BARRIER; break; }
+    double S = F.total(0, F.rb1);
+    F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                    // V2
+    if (!F.sync(51)) { status = ST_BARRIER; break; }
+    for (int i = a.iters - 1; i >= 0; --i) {
+      const bool first = i == a.iters - 1;
+      {
+        EpiPTh<T> e; e.P = F.ptrs(); e.zbar = first ? nullptr : zbuf; e.s_q1 = (T)(S / nout);
+        if (i > 0) F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 1);               // V3
+        else F.rows<1, 0>(F.rb1, F.Sa, nullptr, e, 1);
+      }
+      if (!F.sync(52)) { status = ST_BARRIER; break; }
+      const double tot = F.total(1, F.rb1);
+      sbar += N / nout * tot;
+      if (i == 0) {
+        EpiPTout<T> e; e.P = F.ptrs(); e.dst = a.hin_bar; e.t_q = (T)(tot / nout);
+        F.rows<0, 0>(F.rb1, nullptr, nullptr, e, -1);
+        break;
+      }
+      F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                  // V4
+      if (!F.sync(53)) { status = ST_BARRIER; break; }
+      {
+        EpiPTg<T> e; e.P = F.ptrs(); e.zbuf = zbuf; e.t_q = (T)(tot / nout);
+        F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                          // V5
+      }
+      if (!F.sync(54)) { status = ST_BARRIER; break; }
+      S = F.total(0, F.rb1);
+      F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                  // V6
+      if (!F.sync(55)) { status = ST_BARRIER; break; }
+    }
+  } while (false);
+  if (leader) {
+    *a.sbar = sbar;
+    st->warm_valid = 0; st->com_valid = 0; st->hd_sel = 0; st->A_prev = 0.0; st->A_com = 0.0;
+    st->status = status;
+  }
+}
+
+cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
+                                double* sbar, int iters, cudaStream_t s) {
+  const Desc* dg = d.dev;
+  AdjArgs a{v, hin_bar, sbar, iters};
+  void* args[] = {&dg, &a};
+  const size_t smem = film_smem_bytes(precision);
+  const void* fn = precision ? (const void*)film_adjoint_kernel<float> : (const void*)film_adjoint_kernel<double>;
+  cudaError_t e = precision
+      ? cudaFuncSetAttribute(film_adjoint_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+      : cudaFuncSetAttribute(film_adjoint_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(fn, dim3(d.grid), dim3(NT), args, smem, s);
+}
+
+}  // namespace mf

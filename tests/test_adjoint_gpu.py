@@ -1,0 +1,61 @@
+"""The transposed outside iteration (the linear core of the film right-hand side's
+vector-Jacobian product) on the GPU, against the adjoint oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import film_workload, oracle_of, rel_l2
+from oracle.adjoint2d import FilmAdjoint
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1801_04869_gb300 import native  # noqa: E402
+
+
+def _workload(case):
+    if case == "square_fp64":
+        return W.square_film_128(precision=0), 1e-9
+    if case == "square_fp32":
+        return W.square_film_128(precision=1), 2e-4
+    return film_workload(256, 64, L=(4.0, 1.0), shape="disk", radius=0.8, hole=(0.3, 0.1, 0.25),
+                         n=30.0, rho_out=5.0), 1e-9
+
+
+@pytest.mark.parametrize("iters", [1, 3, 6])
+@pytest.mark.parametrize("case", ["square_fp64", "square_fp32", "disk_hole_nonsquare_fp64"])
+def test_transposed_outside_iteration_matches_oracle(case, iters):
+    wl, tol = _workload(case)
+    o = oracle_of(wl)
+    adj = FilmAdjoint(o, iters)
+    v = W.rng(41 + iters).standard_normal((wl.ny, wl.nx))
+    hb_ref, sb_ref = adj.P_T(v)
+    p = native.from_workload(wl)
+    hb, sb = p.mf_film_outside_vjp(torch.as_tensor(v, device="cuda"), iters)
+    hb = hb.cpu().numpy()
+    assert rel_l2(hb, hb_ref) < tol
+    assert abs(sb - sb_ref) <= tol * abs(sb_ref)
+    assert np.all(hb[wl.mask == 0] == 0.0)
+    # the dot-product identity with the oracle's forward iteration, on the GPU's transpose
+    r = W.rng(50 + iters)
+    x = np.where(wl.mask != 0, r.standard_normal((wl.ny, wl.nx)), 0.0)
+    s = 0.3
+    lhs = float((adj.P(x, s) * v).sum())
+    assert abs(lhs - (float((x * hb).sum()) + s * sb)) <= 10 * tol * (abs(lhs) + 1.0)
+
+
+def test_refused_for_bulk_and_for_films_without_free_space():
+    cube = native.from_workload(W.cube_bulk(16, precision=0))
+    v = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(native.MFError) as e:
+        cube.mf_film_outside_vjp(v, 2)
+    assert e.value.status == native.MF_ERR_ARG
+    wl = film_workload(32, 32, L=(1.0, 1.0), ax=5.0, ay=5.0)         # the film fills the box
+    assert (wl.mask != 0).all()
+    p = native.from_workload(wl)
+    with pytest.raises(native.MFError) as e:
+        p.mf_film_outside_vjp(torch.zeros((32, 32), dtype=torch.float64, device="cuda"), 2)
+    assert e.value.status == native.MF_ERR_ARG
