@@ -207,6 +207,18 @@ mf_status mf_get_info(mf_problem* pb, mf_info* out);
 mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
                               double* sbar);
 
+/* Vector-Jacobian product of a film's right-hand side f(g; jc, h_e_dot) (Eqs. 2-4 and 9-12)
+   with a cold-started, fixed-count outside iteration (as mf_film_outside_vjp): given the state
+   d_g and the cotangent d_v of f (device FP64, nx*ny each), writes the cotangents of g to
+   d_gbar and of the per-cell critical current density to d_jcbar (device FP64, nx*ny; zero
+   outside the superconductor), and that of h_e_dot to *sbar (host, may be NULL).  The power law
+   is linearised as de/dj = rho (I + (n-1) j^ j^T) in the film (rho_out I elsewhere) and
+   de/djc = -(n/jc) e.  One persistent launch on the problem's stream; waits for it; clears the
+   warm start.  MF_ERR_ARG for a bulk problem or a film without free space.  The adjoint has no
+   counterpart in the paper. */
+mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const double* d_v,
+                          double* d_gbar, double* d_jcbar, double* sbar);
+
 /* Checkpoints: everything a continuation reads — the integrator state and counters, the six
    FP64 state/derivative buffers (with the first-same-as-last derivative), the outside
    iteration's warm start, the step log, and the work-item shape and launch width.  Restoring a

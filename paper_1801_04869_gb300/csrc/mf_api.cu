@@ -35,7 +35,8 @@ struct mf_problem {
 namespace mf {
 // transposed outside iteration of a film (csrc/mf_film_adjoint.cu)
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
-                                double* sbar, int iters, cudaStream_t s);
+                                double* sbar, int iters, const double* g, double* gbar,
+                                double* jcbar, cudaStream_t s);
 }  // namespace mf
 
 namespace {
@@ -912,18 +913,18 @@ mf_status mf_checkpoint_restore(mf_problem* pb, const void* src) {
   return MF_OK;
 }
 
-mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
-                              double* sbar) {
-  Range range_("mf_film_outside_vjp");
-  if (!pb || !d_v || !d_hin_bar || iters < 1) return MF_ERR_ARG;
+// one launch of the film's adjoint kernel: the outside iteration alone (g null) or the whole
+// right-hand side's vector-Jacobian product
+static mf_status film_adjoint(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
+                              const double* d_g, double* d_gbar, double* d_jcbar, double* sbar) {
   if (pb->d.dim != 2 || pb->d.nout <= 0) {
-    pb->err = "the transposed outside iteration needs a film with free space";
+    pb->err = "the film adjoint needs a film with free space";
     return MF_ERR_ARG;
   }
   MF_CUDA(pb, cudaSetDevice(pb->device));
   MF_CUDA(pb, cudaMemsetAsync(pb->d.gb, 0, sizeof(GridBarrier), pb->stream));
   cudaError_t e = film_adjoint_launch(pb->d.precision, pb->d, d_v, d_hin_bar, pb->scratch_m, iters,
-                                      pb->stream);
+                                      d_g, d_gbar, d_jcbar, pb->stream);
   if (e != cudaSuccess) return cuda_fail(pb, e, "adjoint kernel launch");
   mf_status r = launch_finish(pb);
   if (r == MF_OK && sbar) {
@@ -931,6 +932,20 @@ mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, doub
     MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
   }
   return r;
+}
+
+mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
+                              double* sbar) {
+  Range range_("mf_film_outside_vjp");
+  if (!pb || !d_v || !d_hin_bar || iters < 1) return MF_ERR_ARG;
+  return film_adjoint(pb, iters, d_v, d_hin_bar, nullptr, nullptr, nullptr, sbar);
+}
+
+mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const double* d_v,
+                          double* d_gbar, double* d_jcbar, double* sbar) {
+  Range range_("mf_film_rhs_vjp");
+  if (!pb || !d_g || !d_v || !d_gbar || !d_jcbar || iters < 1) return MF_ERR_ARG;
+  return film_adjoint(pb, iters, d_v, nullptr, d_g, d_gbar, d_jcbar, sbar);
 }
 
 mf_status mf_get_info(mf_problem* pb, mf_info* out) {

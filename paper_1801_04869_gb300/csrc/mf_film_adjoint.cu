@@ -17,15 +17,129 @@
 //       S_{i-1} = sum gbar_{i-1};   sbar += (N / n_out) tot_i
 //   end hbar_in = conductor * (hbar_0 - tot_0 / n_out),  sbar += (N / n_out) tot_0
 // The h_dot buffers of the warm start hold hbar and zbar, so the warm start is cleared.
+//
+// The full vector-Jacobian product of f(g; jc, h_e_dot) adds the nonlinear ends around it:
+//   j = (d_y g, -d_x g) is recomputed from g (Eq. 2; gradient column pass at the start, stored
+//   as two real fields), r = -conductor * hbar_in, ebar = (d_y r, -d_x r) (the transposed
+//   -curl of Eq. 4 is the smoothed gradient column pass), the linearised power law
+//   jbar = rho (ebar + (n - 1) j^ (j^ . ebar)) in the film and rho_out ebar elsewhere, with
+//   jcbar = -(n / jc) ebar . e in the film (Eq. 3), and gbar = d_x jbar_y - d_y jbar_x, which is
+//   minus the -curl column pass of jbar.
 #include "mf_film.cuh"
 
 namespace mf {
 
 struct AdjArgs {
   const double* v;      // cotangent of g_dot (FP64, ncell)
-  double* hin_bar;      // cotangent of h_dot_in (FP64, ncell; 0 on free space)
+  double* hin_bar;      // cotangent of h_dot_in (FP64, ncell; 0 on free space); outside only
   double* sbar;         // cotangent of h_e_dot (FP64 scalar)
   int iters;
+  const double* g;      // full product: the state g (FP64, ncell); null: the outside iteration only
+  double* gbar;         // full product: cotangent of g (FP64, ncell)
+  double* jcbar;        // full product: cotangent of the jc map (FP64, ncell; 0 outside the film)
+};
+
+// full product, V1: gbar_{I-1} = conductor * v (with its sum) and g, forward of both
+template <typename T>
+struct EpiPT0g : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  const double* v;
+  const double* g;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<double> x = ld4(v + i);
+    const V4<double> y = ld4(g + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T gb = mask_at(m, q) != 0 ? (T)x.v[q] : (T)0;
+      this->acc += gb;
+      out[0].v[q] = gb;
+      out[1].v[q] = (T)y.v[q];
+    }
+  }
+};
+
+// full product: j = (d_y g, -d_x g) stored as two real fields
+template <typename T>
+struct EpiStoreJ : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  T* jx;
+  T* jy;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
+    V4<T> a, b;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { a.v[q] = in[1].v[q]; b.v[q] = -in[0].v[q]; }
+    st4(jx + i, a);
+    st4(jy + i, b);
+  }
+};
+
+// full product: r = -conductor * hbar_in = -conductor * (hbar_0 - tot_0/n_out), forward
+template <typename T>
+struct EpiRbar : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  T t_q;
+  __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    const V4<T> h = ld4(P.hd + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[0].v[q] = mask_at(m, q) != 0 ? -(h.v[q] - t_q) : (T)0;
+  }
+};
+
+// full product: ebar = (d_y r, -d_x r); linearised power law -> jbar (forward), jcbar
+template <typename T>
+struct EpiPowVJP : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  const T* jx;
+  const T* jy;
+  double* jcbar;
+  T n, e0, jc, rho_out;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const uchar4 m = ldmask4(P.mask + i);
+    V4<T> jcl;
+    if (P.jcmap) jcl = ldg4(P.jcmap + i);
+    else jcl = V4<T>{{jc, jc, jc, jc}};
+    const V4<T> ax = ld4(jx + i), ay = ld4(jy + i);
+    V4<double> cb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T ex = in[1].v[q], ey = -in[0].v[q];                 // transposed -curl
+      const T x = ax.v[q], y = ay.v[q];
+      const T j2 = x * x + y * y;
+      const int mq = mask_at(m, q);
+      const T rho = resistivity<T>(j2, jcl.v[q], mq, n, e0, rho_out);
+      T bx = rho * ex, by = rho * ey;
+      double c = 0.0;
+      if (mq == 1) {
+        if (j2 > (T)0) {
+          const T inv = (T)1 / sqrt(j2);
+          const T ux = x * inv, uy = y * inv;
+          const T pr = (n - (T)1) * rho * (ux * ex + uy * ey);
+          bx += pr * ux;
+          by += pr * uy;
+        }
+        c = -(double)(n / jcl.v[q]) * (double)(rho * (ex * x + ey * y));
+      }
+      out[0].v[q] = bx;
+      out[1].v[q] = by;
+      cb.v[q] = c;
+    }
+    st4(jcbar + i, cb);
+  }
+};
+
+// full product: gbar = -(the -curl pass of jbar)
+template <typename T>
+struct EpiGbar : EpiBase<T, T> {
+  FilmPtrs<T> P;
+  double* dst;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
+    V4<double> r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r.v[q] = -(double)in[0].v[q];
+    st4(dst + i, r);
+  }
 };
 
 // V1: gbar_{I-1} = conductor * v, and its sum
@@ -124,15 +238,30 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
   T* const zbuf = (T*)d.hd2;
   int status = ST_OK;
   double sbar = 0.0;
+  const bool full = a.g != nullptr;
+  T* const jx = (T*)d.u;                         // j for the full product: the raw g_dot buffer
+  T* const jy = (T*)(F.Sb + 2 * F.nspec);        // and the third field of Sb, as real storage
   do {
-    {
+    double S;
+    if (full) {
+      EpiPT0g<T> e; e.P = F.ptrs(); e.v = a.v; e.g = a.g;
+      F.rows<0, 2>(F.rb2, nullptr, F.Sa, e, 0);                         // V1 (+ g)
+      if (!F.sync(60)) { status = ST_BARRIER; break; }
+      S = F.total(0, F.rb2);
+    } else {
       EpiPT0<T> e; e.P = F.ptrs(); e.v = a.v;
       F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, 0);                         // V1
+      if (!F.sync(50)) { status = ST_BARRIER; break; }
+      S = F.total(0, F.rb1);
     }
-    if (!F.sync(50)) { status = ST_BARRIER; break; }
-    double S = F.total(0, F.rb1);
     F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                    // V2
+    if (full) F.cols(F.Sa + F.nspec, 1, F.Sa + F.nspec, 2, OP_GRAD);    // grad g -> Sa 1, 2
     if (!F.sync(51)) { status = ST_BARRIER; break; }
+    if (full) {
+      EpiStoreJ<T> e; e.P = F.ptrs(); e.jx = jx; e.jy = jy;
+      F.rows<2, 0>(F.rb2, F.Sa + F.nspec, nullptr, e, -1);              // j (Eq. 2)
+      if (!F.sync(61)) { status = ST_BARRIER; break; }
+    }
     for (int i = a.iters - 1; i >= 0; --i) {
       const bool first = i == a.iters - 1;
       {
@@ -144,8 +273,30 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
       const double tot = F.total(1, F.rb1);
       sbar += N / nout * tot;
       if (i == 0) {
-        EpiPTout<T> e; e.P = F.ptrs(); e.dst = a.hin_bar; e.t_q = (T)(tot / nout);
-        F.rows<0, 0>(F.rb1, nullptr, nullptr, e, -1);
+        if (!full) {
+          EpiPTout<T> e; e.P = F.ptrs(); e.dst = a.hin_bar; e.t_q = (T)(tot / nout);
+          F.rows<0, 0>(F.rb1, nullptr, nullptr, e, -1);
+          break;
+        }
+        {
+          EpiRbar<T> e; e.P = F.ptrs(); e.t_q = (T)(tot / nout);
+          F.rows<0, 1>(F.rb1, nullptr, F.Sb, e, -1);                    // r
+        }
+        if (!F.sync(62)) { status = ST_BARRIER; break; }
+        F.cols(F.Sb, 1, F.Sb, 2, OP_GRAD);                              // grad r -> Sb 0, 1
+        if (!F.sync(63)) { status = ST_BARRIER; break; }
+        {
+          EpiPowVJP<T> e; e.P = F.ptrs(); e.jx = jx; e.jy = jy; e.jcbar = a.jcbar;
+          e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+          F.rows<2, 2>(F.rb2, F.Sb, F.Sa, e, -1);                       // jbar, jcbar (Eq. 3)
+        }
+        if (!F.sync(64)) { status = ST_BARRIER; break; }
+        F.cols(F.Sa, 2, F.Sa, 1, OP_CURLNEG);                           // -curl jbar
+        if (!F.sync(65)) { status = ST_BARRIER; break; }
+        {
+          EpiGbar<T> e; e.P = F.ptrs(); e.dst = a.gbar;
+          F.rows<1, 0>(F.rb1, F.Sa, nullptr, e, -1);                    // gbar
+        }
         break;
       }
       F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                  // V4
@@ -168,9 +319,10 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
 }
 
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
-                                double* sbar, int iters, cudaStream_t s) {
+                                double* sbar, int iters, const double* g, double* gbar,
+                                double* jcbar, cudaStream_t s) {
   const Desc* dg = d.dev;
-  AdjArgs a{v, hin_bar, sbar, iters};
+  AdjArgs a{v, hin_bar, sbar, iters, g, gbar, jcbar};
   void* args[] = {&dg, &a};
   const size_t smem = film_smem_bytes(precision);
   const void* fn = precision ? (const void*)film_adjoint_kernel<float> : (const void*)film_adjoint_kernel<double>;

@@ -28,7 +28,7 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
            "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
            "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
-           "mf_checkpoint_restore", "mf_film_outside_vjp"]
+           "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp"]
 
 
 class mf_params(ctypes.Structure):
@@ -106,6 +106,7 @@ def load() -> ctypes.CDLL:
         "mf_checkpoint_save": (ctypes.c_int, [vp, vp]),
         "mf_checkpoint_restore": (ctypes.c_int, [vp, vp]),
         "mf_film_outside_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, dp]),
+        "mf_film_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, dp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -289,6 +290,16 @@ class Problem:
         sb = ctypes.c_double(0.0)
         self._check(self.lib.mf_film_outside_vjp(self.h, iters, _dptr(v), _dptr(out), ctypes.byref(sb)))
         return out, sb.value
+
+    def mf_film_rhs_vjp(self, g, v, iters: int):
+        """Cotangents (of g and of the jc map as device tensors, of h_e_dot as a float) of the
+        film right-hand side with a cold-started, fixed-count outside iteration."""
+        import torch
+        gbar, jcbar = torch.empty_like(v), torch.empty_like(v)
+        sb = ctypes.c_double(0.0)
+        self._check(self.lib.mf_film_rhs_vjp(self.h, iters, _dptr(g), _dptr(v), _dptr(gbar),
+                                             _dptr(jcbar), ctypes.byref(sb)))
+        return gbar, jcbar, sb.value
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()

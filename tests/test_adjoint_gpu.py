@@ -1,5 +1,5 @@
-"""The transposed outside iteration (the linear core of the film right-hand side's
-vector-Jacobian product) on the GPU, against the adjoint oracle, through the C ABI."""
+"""The film right-hand side's vector-Jacobian product on the GPU — the transposed outside
+iteration alone and the whole product — against the adjoint oracle, through the C ABI."""
 import numpy as np
 import pytest
 
@@ -45,6 +45,31 @@ def test_transposed_outside_iteration_matches_oracle(case, iters):
     s = 0.3
     lhs = float((adj.P(x, s) * v).sum())
     assert abs(lhs - (float((x * hb).sum()) + s * sb)) <= 10 * tol * (abs(lhs) + 1.0)
+
+
+@pytest.mark.parametrize("case", ["square_fp64", "square_fp32", "disk_hole_nonsquare_fp64"])
+def test_rhs_vjp_matches_oracle(case):
+    """Cotangents of g, of the jc map and of h_e_dot, with a jc map and a near-critical state so
+    that the linearised power law (n - 1 = 18 or 29) carries the result."""
+    wl, tol = _workload(case)
+    wl.jc_map = W.jc_map_lognormal((wl.ny, wl.nx), seed=44, sigma=0.05)
+    o = oracle_of(wl)
+    iters = 4
+    adj = FilmAdjoint(o, iters)
+    jc = np.array(o.jc)
+    g = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=45, amplitude=1.0)
+    v = W.rng(46).standard_normal((wl.ny, wl.nx))
+    _, tape = adj.rhs(g, jc, 0.3)
+    gb_ref, cb_ref, sb_ref = adj.rhs_vjp(tape, jc, v)
+    p = native.from_workload(wl)
+    gb, cb, sb = p.mf_film_rhs_vjp(torch.as_tensor(g, device="cuda"), torch.as_tensor(v, device="cuda"),
+                                   iters)
+    gb, cb = gb.cpu().numpy(), cb.cpu().numpy()
+    assert np.abs(cb_ref).max() > 1e-3 * np.abs(gb_ref).max()      # the jc term is not negligible
+    assert rel_l2(gb, gb_ref) < tol
+    assert rel_l2(cb, cb_ref) < tol
+    assert np.all(cb[wl.mask != 1] == 0.0)
+    assert abs(sb - sb_ref) <= tol * abs(sb_ref)
 
 
 def test_refused_for_bulk_and_for_films_without_free_space():
