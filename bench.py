@@ -206,6 +206,45 @@ def autotune_leg(native, W, torch, n_grid: int):
             "timing": "CUDA events, 5 launches of one right-hand side with 4 forced outside iterations"}
 
 
+def adjoint_leg(native, W, torch, reps: int = 10, iters: int = 5):
+    """Secondary line: the film right-hand side's vector-Jacobian product (mf_film_rhs_vjp) on
+    the adjoint workload's film — 512 x 512 cells in a 1024^2 grid, n = 30, lognormal jc map
+    (sigma 0.2), FP32 transforms — against the forward right-hand side with the same
+    cold-started, fixed iteration count.  CUDA events on the library's stream."""
+    n_grid = 1024
+    L = 2.0
+    mask = W.film_mask(n_grid, n_grid, L, L, "rect", ax=1.0, ay=1.0)
+    wl = W.Workload("square_film_512_in_1024", 2, n_grid, n_grid, 1, L, L, 0.0, mask, n=30.0,
+                    rho_out=1.0, precision=1, t0=0.0, t1=1.0, he_knots=((0.0, 1.0), (0.0, 0.5)))
+    wl.jc_map = W.jc_map_lognormal((n_grid, n_grid), seed=5, sigma=0.2)
+    p = native.from_workload(wl)
+    g = torch.as_tensor(W.film_state(mask, L, L, seed=6, amplitude=1.0), device="cuda")
+    v = torch.as_tensor(W.rng(7).standard_normal((n_grid, n_grid)), device="cuda")
+    out = torch.empty_like(g)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(p.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(p.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def fwd():
+        p.mf_reset_warm()
+        p.mf_rhs(0.3, g, out, force_iters=iters, allow_noconv=True)
+
+    ms_vjp = timed(lambda: p.mf_film_rhs_vjp(g, v, iters))
+    ms_fwd = timed(fwd)
+    return {"workload": wl.name, "outside_iterations": iters, "ms_per_vjp": ms_vjp,
+            "ms_per_rhs": ms_fwd, "vjp_per_rhs": ms_vjp / ms_fwd, "value": 1000.0 / ms_vjp,
+            "unit": "VJP/s", "transforms": "f32",
+            "timing": "CUDA events over repeated single launches (each waits for its status)"}
+
+
 def batch_leg(native, W, torch, count: int = 256, steps: int = 6, warmup: int = 2,
               max_side: int = 512):
     """Secondary line: a sweep of `count` independent films (seeded shapes, sides 64..512 cells,
@@ -336,7 +375,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the bulk and full-ramp legs")
     ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
-    ap.add_argument("--only", choices=["batch"], help="run one secondary leg alone (profiling)")
+    ap.add_argument("--only", choices=["batch", "adjoint"], help="run one secondary leg alone")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max-side", type=int, default=512)
     args = ap.parse_args()
@@ -361,6 +400,10 @@ def main():
         if rank == 0:
             print(json.dumps(batch_leg(native, W, torch, count=args.batch_count,
                                        max_side=args.batch_max_side)))
+        return
+    if args.only == "adjoint":
+        if rank == 0:
+            print(json.dumps(adjoint_leg(native, W, torch)))
         return
     dist = None
     if world > 1:
@@ -446,6 +489,7 @@ def main():
         bulk = bulk_leg(native, W, torch) if not args.no_extra else None
         bulk_256 = bulk_leg(native, W, torch, n_grid=256) if not args.no_extra else None
         tune = autotune_leg(native, W, torch, args.grid) if not args.no_extra else None
+        adj = adjoint_leg(native, W, torch) if not args.no_extra else None
         batch = batch_leg(native, W, torch) if not args.no_extra else None
         ramps = [full_ramp_leg(native, W, torch, prec) for prec in (0, 1)] if not args.no_extra else None
         line = {
@@ -477,6 +521,7 @@ def main():
             "bulk": bulk,
             "bulk_256": bulk_256,
             "autotune": tune,
+            "adjoint": adj,
             "batch": batch,
             "full_ramp": ramps,
         }
