@@ -219,6 +219,26 @@ mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, doub
 mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const double* d_v,
                           double* d_gbar, double* d_jcbar, double* sbar);
 
+/* Gradient of a film solve.  The map: from the state d_g0 (device FP64, nx*ny), n_steps
+   Bogacki-Shampine steps with the given times and sizes (host t_steps[i], h_steps[i]; every step
+   inside one segment of the h_e knots, all accepted: y <- y + h (2/9 k1 + 1/3 k2 + 4/9 k3)),
+   each right-hand side with a cold-started outside iteration of exactly `iters` iterations; the
+   loss L = 1/2 dx dy sum (h_z(T) - target)^2 with h_z = h_e + F^-1[(|k|/2) F g] (end of Section
+   2.1) at T = t_steps[n-1] + h_steps[n-1] and d_target device FP64 (nx*ny).  Writes *loss (host),
+   dL/djc per cell to d_jcbar (device FP64, nx*ny; zero outside the superconductor) and dL/dv_k
+   for the knot values of h_e to knots_bar (host, he_knots entries).  The forward keeps every
+   step's state in d_work (device, at least mf_film_solve_gradient_work_bytes bytes); the reverse
+   sweep recomputes each step's stages from it and runs mf_film_rhs_vjp three times per step.
+   Runs on the problem's stream and waits; the solver's own state is untouched but its warm
+   start is cleared and its counters count these evaluations.  MF_ERR_ARG for a bulk problem, a
+   film without free space, a sinusoidal h_e or a step across a knot; MF_ERR_WORKSPACE for a
+   short work buffer.  The adjoint has no counterpart in the paper. */
+size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps);
+mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const double* t_steps,
+                                 const double* h_steps, const double* d_g0, const double* d_target,
+                                 void* d_work, size_t work_bytes, double* d_jcbar,
+                                 double* knots_bar, double* loss);
+
 /* Checkpoints: everything a continuation reads — the integrator state and counters, the six
    FP64 state/derivative buffers (with the first-same-as-last derivative), the outside
    iteration's warm start, the step log, and the work-item shape and launch width.  Restoring a

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <initializer_list>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -37,6 +38,9 @@ namespace mf {
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
                                 double* sbar, int iters, const double* g, double* gbar,
                                 double* jcbar, cudaStream_t s);
+cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
+                        double b, cudaStream_t s);
+cudaError_t adj_sums(long long n, const double* x, double* out, cudaStream_t s);
 }  // namespace mf
 
 namespace {
@@ -946,6 +950,142 @@ mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const do
   Range range_("mf_film_rhs_vjp");
   if (!pb || !d_g || !d_v || !d_gbar || !d_jcbar || iters < 1) return MF_ERR_ARG;
   return film_adjoint(pb, iters, d_v, nullptr, d_g, d_gbar, d_jcbar, sbar);
+}
+
+size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps) {
+  if (!pb || n_steps < 1 || pb->d.dim != 2) return 0;
+  return ((size_t)n_steps + 11) * (size_t)pb->d.ncell * sizeof(double) + 64;
+}
+
+mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const double* t_steps,
+                                 const double* h_steps, const double* d_g0, const double* d_target,
+                                 void* d_work, size_t work_bytes, double* d_jcbar,
+                                 double* knots_bar, double* loss) {
+  Range range_("mf_film_solve_gradient");
+  if (!pb || iters < 1 || n_steps < 1 || !t_steps || !h_steps || !d_g0 || !d_target || !d_work ||
+      !d_jcbar || !knots_bar || !loss)
+    return MF_ERR_ARG;
+  if (pb->d.dim != 2 || pb->d.nout <= 0 || pb->p.he_knots < 2) {
+    pb->err = "the solve gradient needs a film with free space and a piecewise-linear h_e";
+    return MF_ERR_ARG;
+  }
+  if (work_bytes < mf_film_solve_gradient_work_bytes(pb, n_steps)) {
+    pb->err = "work buffer smaller than mf_film_solve_gradient_work_bytes";
+    return MF_ERR_WORKSPACE;
+  }
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  const int K = pb->p.he_knots;
+  std::vector<double> kn(2 * K);
+  MF_CUDA(pb, cudaMemcpyAsync(kn.data(), pb->d.he_t, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  const double* kt = kn.data();
+  const double* kv = kn.data() + K;
+  // each step inside one waveform segment
+  std::vector<int> seg(n_steps);
+  for (int i = 0; i < n_steps; ++i) {
+    const double t = t_steps[i], h = h_steps[i];
+    int k = (int)(std::upper_bound(kt, kt + K, t) - kt) - 1;
+    if (!(h > 0.0) || k < 0 || k >= K - 1 || t + h > kt[k + 1] * (1.0 + 1e-15) + 1e-300) {
+      pb->err = "every step must lie inside one segment of the h_e knots";
+      return MF_ERR_ARG;
+    }
+    seg[i] = k;
+  }
+  const long long n = pb->d.ncell;
+  const cudaStream_t st = pb->stream;
+  double* Y = (double*)d_work;                 // states Y_0 .. Y_N
+  double* K1 = Y + (size_t)(n_steps + 1) * n;
+  double* K2 = K1 + n;
+  double* K3 = K2 + n;
+  double* Y2 = K3 + n;
+  double* Y3 = Y2 + n;
+  double* LAM = Y3 + n;
+  double* V = LAM + n;
+  double* G2 = V + n;
+  double* G3 = G2 + n;
+  double* TMP = G3 + n;
+  double* SC = TMP + n;                         // 2 device scalars
+  const double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
+  auto lin = [&](double* out, std::initializer_list<std::pair<const double*, double>> terms,
+                 double c = 0.0) -> mf_status {
+    const double* x[4];
+    double co[4];
+    int m = 0;
+    for (const auto& tc : terms) { x[m] = tc.first; co[m] = tc.second; ++m; }
+    cudaError_t e = adj_lincomb(n, out, m, x, co, c, st);
+    return e == cudaSuccess ? MF_OK : cuda_fail(pb, e, "lincomb");
+  };
+  // f with a cold start and the fixed count (a forced count may end above the stop test)
+  auto f = [&](const double* y, double* out, int i) -> mf_status {
+    mf_status r = mf_reset_warm(pb);
+    if (r != MF_OK) return r;
+    r = mf_rhs_ex(pb, t_steps[i], seg[i], y, out, iters, nullptr);
+    return r == MF_ERR_NOCONV ? MF_OK : r;
+  };
+#define MF_TRY(x) do { mf_status r_ = (x); if (r_ != MF_OK) return r_; } while (0)
+  MF_CUDA(pb, cudaMemcpyAsync(Y, d_g0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // forward over the frozen steps, keeping every state
+  for (int i = 0; i < n_steps; ++i) {
+    const double h = h_steps[i];
+    double* y = Y + (size_t)i * n;
+    MF_TRY(f(y, K1, i));
+    MF_TRY(lin(Y2, {{y, 1.0}, {K1, 0.5 * h}}));
+    MF_TRY(f(Y2, K2, i));
+    MF_TRY(lin(Y3, {{y, 1.0}, {K2, 0.75 * h}}));
+    MF_TRY(f(Y3, K3, i));
+    MF_TRY(lin(y + n, {{y, 1.0}, {K1, h * b1}, {K2, h * b2}, {K3, h * b3}}));
+  }
+  // loss and the cotangent of the final state: res = h_z(T) - target, lambda = dA K_h res
+  const double T = t_steps[n_steps - 1] + h_steps[n_steps - 1];
+  int kT = (int)(std::upper_bound(kt, kt + K, T) - kt) - 1;
+  kT = std::min(std::max(kT, 0), K - 2);
+  const double wT = (T - kt[kT]) / (kt[kT + 1] - kt[kT]);
+  const double heT = kv[kT] + wT * (kv[kT + 1] - kv[kT]);
+  const double dA = pb->d.dx * pb->d.dy;
+  MF_TRY(mf_readout_of(pb, MF_READ_HZ, T, Y + (size_t)n_steps * n, TMP));
+  MF_TRY(lin(TMP, {{TMP, 1.0}, {d_target, -1.0}}));
+  double sums[2];
+  {
+    cudaError_t e = adj_sums(n, TMP, SC, st);
+    if (e != cudaSuccess) return cuda_fail(pb, e, "sums");
+  }
+  MF_CUDA(pb, cudaMemcpyAsync(sums, SC, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MF_CUDA(pb, cudaStreamSynchronize(st));
+  *loss = 0.5 * dA * sums[1];
+  for (int k = 0; k < K; ++k) knots_bar[k] = 0.0;
+  knots_bar[kT] += (1.0 - wT) * dA * sums[0];
+  knots_bar[kT + 1] += wT * dA * sums[0];
+  MF_TRY(mf_readout_of(pb, MF_READ_HZ, T, TMP, V));                  // h_e(T) + K_h res
+  MF_TRY(lin(LAM, {{V, dA}}, -dA * heT));
+  MF_CUDA(pb, cudaMemsetAsync(d_jcbar, 0, n * sizeof(double), st));
+  // reverse sweep: recompute the stages from the kept state, then the three products
+  for (int i = n_steps - 1; i >= 0; --i) {
+    const double h = h_steps[i];
+    const double* y = Y + (size_t)i * n;
+    MF_TRY(f(y, K1, i));
+    MF_TRY(lin(Y2, {{y, 1.0}, {K1, 0.5 * h}}));
+    MF_TRY(f(Y2, K2, i));
+    MF_TRY(lin(Y3, {{y, 1.0}, {K2, 0.75 * h}}));
+    double sb[3];
+    MF_TRY(lin(V, {{LAM, h * b3}}));
+    MF_TRY(mf_film_rhs_vjp(pb, iters, Y3, V, G3, TMP, &sb[2]));        // k3 = f(Y3)
+    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
+    MF_TRY(lin(V, {{LAM, h * b2}, {G3, 0.75 * h}}));
+    MF_TRY(mf_film_rhs_vjp(pb, iters, Y2, V, G2, TMP, &sb[1]));        // k2 = f(Y2)
+    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
+    MF_TRY(lin(V, {{LAM, h * b1}, {G2, 0.5 * h}}));
+    MF_TRY(mf_film_rhs_vjp(pb, iters, y, V, K3, TMP, &sb[0]));         // k1 = f(Y_i)
+    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
+    MF_TRY(lin(LAM, {{LAM, 1.0}, {G3, 1.0}, {G2, 1.0}, {K3, 1.0}}));
+    const int k = seg[i];
+    const double dt = kt[k + 1] - kt[k];
+    const double sbar = sb[0] + sb[1] + sb[2];                         // h_e_dot = slope of k
+    knots_bar[k + 1] += sbar / dt;
+    knots_bar[k] -= sbar / dt;
+  }
+#undef MF_TRY
+  MF_CUDA(pb, cudaStreamSynchronize(st));
+  return MF_OK;
 }
 
 mf_status mf_get_info(mf_problem* pb, mf_info* out) {

@@ -318,6 +318,58 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
   }
 }
 
+// ---- elementwise helpers of the frozen-step adjoint solve (FP64 state vectors) ----
+// out = c0 x0 + c1 x1 + c2 x2 + c3 x3 + b over the first nt terms; out may be x0 (in place)
+__global__ void lincomb_kernel(long long n, double* out, int nt, const double* x0, double c0,
+                               const double* x1, double c1, const double* x2, double c2,
+                               const double* x3, double c3, double b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double s = b;
+    if (nt > 0) s += c0 * x0[i];
+    if (nt > 1) s += c1 * x1[i];
+    if (nt > 2) s += c2 * x2[i];
+    if (nt > 3) s += c3 * x3[i];
+    out[i] = s;
+  }
+}
+
+// out[0] = sum x, out[1] = sum x^2, in a fixed order (one block)
+__global__ void __launch_bounds__(1024) sums_kernel(long long n, const double* x, double* out) {
+  __shared__ double s1[1024], s2[1024];
+  double a = 0.0, b = 0.0;
+  for (long long i = threadIdx.x; i < n; i += 1024) {
+    const double v = x[i];
+    a += v;
+    b += v * v;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] += s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = s1[0]; out[1] = s2[0]; }
+}
+
+cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
+                        double b, cudaStream_t s) {
+  const double* z = nullptr;
+  lincomb_kernel<<<304, 256, 0, s>>>(n, out, nt, nt > 0 ? x[0] : z, nt > 0 ? c[0] : 0.0,
+                                     nt > 1 ? x[1] : z, nt > 1 ? c[1] : 0.0, nt > 2 ? x[2] : z,
+                                     nt > 2 ? c[2] : 0.0, nt > 3 ? x[3] : z, nt > 3 ? c[3] : 0.0, b);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_sums(long long n, const double* x, double* out, cudaStream_t s) {
+  sums_kernel<<<1, 1024, 0, s>>>(n, x, out);
+  return cudaGetLastError();
+}
+
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
                                 double* sbar, int iters, const double* g, double* gbar,
                                 double* jcbar, cudaStream_t s) {

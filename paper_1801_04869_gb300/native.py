@@ -28,7 +28,8 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_run_ramp", "mf_readout", "mf_readout_of", "mf_get_info", "mf_get_log",
            "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
            "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
-           "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp"]
+           "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp",
+           "mf_film_solve_gradient_work_bytes", "mf_film_solve_gradient"]
 
 
 class mf_params(ctypes.Structure):
@@ -107,6 +108,9 @@ def load() -> ctypes.CDLL:
         "mf_checkpoint_restore": (ctypes.c_int, [vp, vp]),
         "mf_film_outside_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, dp]),
         "mf_film_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, dp]),
+        "mf_film_solve_gradient_work_bytes": (ctypes.c_size_t, [vp, ctypes.c_int]),
+        "mf_film_solve_gradient": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp, vp, vp, vp,
+                                                  ctypes.c_size_t, vp, dp, dp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -300,6 +304,22 @@ class Problem:
         self._check(self.lib.mf_film_rhs_vjp(self.h, iters, _dptr(g), _dptr(v), _dptr(gbar),
                                              _dptr(jcbar), ctypes.byref(sb)))
         return gbar, jcbar, sb.value
+
+    def mf_film_solve_gradient(self, g0, target, steps, iters: int, n_knots: int):
+        """(loss, dL/djc as a device tensor, dL/dknot values as a list) of the frozen-step solve
+        over steps = [(t, h), ...]."""
+        import torch
+        n = len(steps)
+        ts = (ctypes.c_double * n)(*[float(t) for t, _ in steps])
+        hs = (ctypes.c_double * n)(*[float(h) for _, h in steps])
+        nb = self.lib.mf_film_solve_gradient_work_bytes(self.h, n)
+        work = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        jcbar = torch.empty_like(g0)
+        kb = (ctypes.c_double * max(n_knots, 1))()
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.mf_film_solve_gradient(self.h, iters, n, ts, hs, _dptr(g0), _dptr(target),
+                                                    _dptr(work), nb, _dptr(jcbar), kb, ctypes.byref(loss)))
+        return loss.value, jcbar, list(kb)[:n_knots]
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()

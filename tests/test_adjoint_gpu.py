@@ -72,6 +72,31 @@ def test_rhs_vjp_matches_oracle(case):
     assert abs(sb - sb_ref) <= tol * abs(sb_ref)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-3)])
+def test_solve_gradient_matches_oracle(precision, tol):
+    """Loss, dL/djc and dL/d(knot values) of a frozen-step solve (6 steps, 4 outside iterations,
+    n = 19, lognormal jc map, near-critical start) against FilmAdjoint.gradient.  FP32
+    transforms: each evaluation is within 2e-4 and the gradient sums 3 products and 3 forward
+    evaluations a step, so 1e-3."""
+    wl = W.square_film_128(precision=precision)
+    wl.he_knots = ((0.0, 0.5, 1.0), (0.0, 0.3, 0.45))
+    wl.jc_map = W.jc_map_lognormal((wl.ny, wl.nx), seed=47, sigma=0.05)
+    o = oracle_of(wl)
+    iters = 4
+    adj = FilmAdjoint(o, iters)
+    jc = np.array(o.jc)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=48, amplitude=1.0)
+    target = W.rng(49).standard_normal((wl.ny, wl.nx)) * 0.01
+    steps = [(0.1 + 0.002 * i, 0.002) for i in range(6)]
+    L_ref, cb_ref, vb_ref = adj.gradient(g0, jc, wl.he_knots[0], wl.he_knots[1], steps, target)
+    p = native.from_workload(wl)
+    L, cb, vb = p.mf_film_solve_gradient(torch.as_tensor(g0, device="cuda"),
+                                         torch.as_tensor(target, device="cuda"), steps, iters, 3)
+    assert abs(L - L_ref) <= tol * abs(L_ref)
+    assert rel_l2(cb.cpu().numpy(), cb_ref) < tol
+    np.testing.assert_allclose(vb, vb_ref, rtol=tol, atol=tol * np.abs(vb_ref).max())
+
+
 def test_refused_for_bulk_and_for_films_without_free_space():
     cube = native.from_workload(W.cube_bulk(16, precision=0))
     v = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
