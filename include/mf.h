@@ -233,6 +233,13 @@ mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const do
    start is cleared and its counters count these evaluations.  MF_ERR_ARG for a bulk problem, a
    film without free space, a sinusoidal h_e or a step across a knot; MF_ERR_WORKSPACE for a
    short work buffer.  The adjoint has no counterpart in the paper. */
+/* Replace the per-cell critical current density (device FP64, nx*ny[*nz]) of a problem that was
+   created with a jc map (MF_ERR_ARG otherwise), or the knot values of a piecewise-linear h_e
+   (host, he_knots entries; the knot times stay).  Both wait for the problem's stream; later
+   calls use the new values.  They let a gradient's parameters change without a new problem. */
+mf_status mf_set_jc_map(mf_problem* pb, const double* d_jc);
+mf_status mf_set_knot_values(mf_problem* pb, const double* h_values);
+
 size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps);
 mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const double* t_steps,
                                  const double* h_steps, const double* d_g0, const double* d_target,

@@ -41,6 +41,7 @@ cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, d
 cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
                         double b, cudaStream_t s);
 cudaError_t adj_sums(long long n, const double* x, double* out, cudaStream_t s);
+cudaError_t adj_to_float(long long n, const double* x, float* y, cudaStream_t s);
 }  // namespace mf
 
 namespace {
@@ -1085,6 +1086,38 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const d
   }
 #undef MF_TRY
   MF_CUDA(pb, cudaStreamSynchronize(st));
+  return MF_OK;
+}
+
+mf_status mf_set_jc_map(mf_problem* pb, const double* d_jc) {
+  if (!pb || !d_jc) return MF_ERR_ARG;
+  if (!pb->d.jcmap) {
+    pb->err = "the problem was created without a jc map";
+    return MF_ERR_ARG;
+  }
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  const long long n = pb->d.ncell;
+  if (pb->d.precision) {
+    cudaError_t e = adj_to_float(n, d_jc, (float*)pb->d.jcmap, pb->stream);
+    if (e != cudaSuccess) return cuda_fail(pb, e, "jc map conversion");
+  } else {
+    MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.jcmap, d_jc, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                pb->stream));
+  }
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  return MF_OK;
+}
+
+mf_status mf_set_knot_values(mf_problem* pb, const double* h_values) {
+  if (!pb || !h_values) return MF_ERR_ARG;
+  if (pb->p.he_knots < 1) {
+    pb->err = "the problem's h_e is not piecewise linear";
+    return MF_ERR_ARG;
+  }
+  MF_CUDA(pb, cudaSetDevice(pb->device));
+  MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.he_v, h_values, pb->p.he_knots * sizeof(double),
+                              cudaMemcpyHostToDevice, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));      // the values are a host buffer
   return MF_OK;
 }
 

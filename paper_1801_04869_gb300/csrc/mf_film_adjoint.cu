@@ -356,6 +356,18 @@ __global__ void __launch_bounds__(1024) sums_kernel(long long n, const double* x
   if (threadIdx.x == 0) { out[0] = s1[0]; out[1] = s2[0]; }
 }
 
+// FP64 -> transform precision copy (a jc map set after creation)
+__global__ void to_float_kernel(long long n, const double* x, float* y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+cudaError_t adj_to_float(long long n, const double* x, float* y, cudaStream_t s) {
+  to_float_kernel<<<304, 256, 0, s>>>(n, x, y);
+  return cudaGetLastError();
+}
+
 cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
                         double b, cudaStream_t s) {
   const double* z = nullptr;

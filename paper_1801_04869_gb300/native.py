@@ -29,7 +29,8 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_last_error", "mf_destroy", "mf_film_rhs_noalloc", "mf_advance_batch",
            "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
            "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp",
-           "mf_film_solve_gradient_work_bytes", "mf_film_solve_gradient"]
+           "mf_film_solve_gradient_work_bytes", "mf_film_solve_gradient", "mf_set_jc_map",
+           "mf_set_knot_values"]
 
 
 class mf_params(ctypes.Structure):
@@ -109,6 +110,8 @@ def load() -> ctypes.CDLL:
         "mf_film_outside_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, dp]),
         "mf_film_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, dp]),
         "mf_film_solve_gradient_work_bytes": (ctypes.c_size_t, [vp, ctypes.c_int]),
+        "mf_set_jc_map": (ctypes.c_int, [vp, vp]),
+        "mf_set_knot_values": (ctypes.c_int, [vp, dp]),
         "mf_film_solve_gradient": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp, vp, vp, vp,
                                                   ctypes.c_size_t, vp, dp, dp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
@@ -320,6 +323,14 @@ class Problem:
         self._check(self.lib.mf_film_solve_gradient(self.h, iters, n, ts, hs, _dptr(g0), _dptr(target),
                                                     _dptr(work), nb, _dptr(jcbar), kb, ctypes.byref(loss)))
         return loss.value, jcbar, list(kb)[:n_knots]
+
+    def mf_set_jc_map(self, jc):
+        """jc: device float64 tensor of the grid's cells."""
+        self._check(self.lib.mf_set_jc_map(self.h, _dptr(jc)))
+
+    def mf_set_knot_values(self, values):
+        v = [float(x) for x in values]
+        self._check(self.lib.mf_set_knot_values(self.h, (ctypes.c_double * len(v))(*v)))
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()

@@ -97,6 +97,47 @@ def test_solve_gradient_matches_oracle(precision, tol):
     np.testing.assert_allclose(vb, vb_ref, rtol=tol, atol=tol * np.abs(vb_ref).max())
 
 
+def test_autograd_wrapper_and_central_differences_of_the_gpu_map():
+    """jc.grad and knots.grad through torch.autograd equal the oracle's gradient, and central
+    differences of the GPU map itself (parameters changed in place with mf_set_jc_map and
+    mf_set_knot_values) agree with them."""
+    from paper_1801_04869_gb300.adjoint import film_solve_loss
+    wl = W.square_film_128(precision=0)
+    wl.he_knots = ((0.0, 0.5, 1.0), (0.0, 0.3, 0.45))
+    wl.jc_map = W.jc_map_lognormal((wl.ny, wl.nx), seed=47, sigma=0.05)
+    o = oracle_of(wl)
+    iters = 4
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=48, amplitude=1.0)
+    target = W.rng(49).standard_normal((wl.ny, wl.nx)) * 0.01
+    steps = [(0.1 + 0.002 * i, 0.002) for i in range(6)]
+    _, cb_ref, vb_ref = FilmAdjoint(o, iters).gradient(g0, np.array(o.jc), wl.he_knots[0],
+                                                       wl.he_knots[1], steps, target)
+    p = native.from_workload(wl)
+    g0d = torch.as_tensor(g0, device="cuda")
+    td = torch.as_tensor(target, device="cuda")
+    jc = torch.tensor(wl.jc_map, dtype=torch.float64, device="cuda", requires_grad=True)
+    kv = torch.tensor(wl.he_knots[1], dtype=torch.float64, requires_grad=True)
+    loss = film_solve_loss(jc, kv, p, g0d, td, steps, iters)
+    loss.backward()
+    assert rel_l2(jc.grad.cpu().numpy(), cb_ref) < 1e-9
+    np.testing.assert_allclose(kv.grad.numpy(), vb_ref, rtol=1e-9, atol=1e-12)
+
+    def L(jcv, kvv):
+        with torch.no_grad():
+            return float(film_solve_loss(jcv, kvv, p, g0d, td, steps, iters))
+
+    eps = 1e-5
+    i = int(np.argmax(np.abs(cb_ref)))
+    e = torch.zeros_like(jc).view(-1)
+    e[i] = eps
+    e = e.view_as(jc)
+    fd = (L(jc.detach() + e, kv.detach()) - L(jc.detach() - e, kv.detach())) / (2 * eps)
+    assert abs(fd - cb_ref.reshape(-1)[i]) <= 1e-6 * abs(fd)
+    d = torch.tensor([0.0, eps, 0.0], dtype=torch.float64)
+    fd = (L(jc.detach(), kv.detach() + d) - L(jc.detach(), kv.detach() - d)) / (2 * eps)
+    assert abs(fd - vb_ref[1]) <= 1e-6 * abs(fd)
+
+
 def test_refused_for_bulk_and_for_films_without_free_space():
     cube = native.from_workload(W.cube_bulk(16, precision=0))
     v = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
