@@ -371,6 +371,7 @@ cudaError_t adj_to_float(long long n, const double* x, float* y, cudaStream_t s)
 cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
                         double b, cudaStream_t s) {
   const double* z = nullptr;
+  // grid-stride: 304 blocks (two per SM of a GB300) cover any length
   lincomb_kernel<<<304, 256, 0, s>>>(n, out, nt, nt > 0 ? x[0] : z, nt > 0 ? c[0] : 0.0,
                                      nt > 1 ? x[1] : z, nt > 1 ? c[1] : 0.0, nt > 2 ? x[2] : z,
                                      nt > 2 ? c[2] : 0.0, nt > 3 ? x[3] : z, nt > 3 ? c[3] : 0.0, b);
