@@ -18,7 +18,8 @@ class FilmSolveLoss(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, jc, knots, problem, g0, target, steps, iters):
-        problem.mf_set_jc_map(jc.detach().to(torch.float64).contiguous())
+        dev = getattr(problem, "device", jc.device)
+        problem.mf_set_jc_map(jc.detach().to(device=dev, dtype=torch.float64).contiguous())
         problem.mf_set_knot_values(knots.detach().cpu().tolist())
         loss, jcbar, kbar = problem.mf_film_solve_gradient(g0, target, steps, iters, knots.numel())
         ctx.save_for_backward(jcbar.view_as(jc), torch.tensor(kbar, dtype=knots.dtype,
