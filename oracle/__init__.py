@@ -4,7 +4,8 @@
 TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's CPU
 baseline may import this package; the library's compute path never calls it and shares no
 code with it.  Every function follows the paper's equations in their order and notation, in
-float64, with numpy.fft as the only library step, and no blocking, fusion or reordering.
+float64, with the discrete Fourier transform (oracle/_fft.py: scipy.fft on the host's
+cores) as the only library step, and no blocking, fusion or reordering.
 
 Modules
   film2d   thin-film right-hand side f(t, g) (Section 2, Eqs. 2-12) and readouts

@@ -25,7 +25,8 @@ Readings where the paper is silent:
 Arrays are (3, nz, ny, nx), component-major (SoA).  Pinned by tests/test_oracle_bulk3d.py:
 curl of trig fields, the closed-form centre field (2/3) m0 of a spherically symmetric Gaussian
 magnetization for Phi, curl Phi[j] = j for divergence-free j, Ohmic linearity, invariants and
-the Bean slab profile.
+the Bean slab profile; by tests/test_oracle_power_law_pins.py: the exact jc and e0 scalings of
+Eq. 13 with a lognormal jc map.
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ import math
 
 import numpy as np
 
+from . import _fft as dft
 from .film2d import wavenumbers
 from .waveform import Waveform
 
@@ -78,11 +80,11 @@ class BulkProblem:
     # ---- operators -----------------------------------------------------------------------
     @staticmethod
     def _fft(v):
-        return [np.fft.fftn(c) for c in v]
+        return [dft.fftn(c) for c in v]
 
     @staticmethod
     def _ifft_re(vh):
-        return np.stack([np.real(np.fft.ifftn(c)) for c in vh])
+        return np.stack([np.real(dft.ifftn(c)) for c in vh])
 
     def curl(self, v: np.ndarray) -> np.ndarray:
         """Gaussian-smoothed spectral curl of a vector field (3, nz, ny, nx)."""

@@ -33,7 +33,11 @@ Readings where the paper is silent:
 Pinned by tests/test_oracle_film2d.py: spectral derivatives and the Gaussian against trig
 closed forms, 2/|k| and |k|/2 against the closed-form field of a Gaussian stream function,
 Eq. 10/11 invariants, linearity of the Ohmic case, the exact decay rate 2 rho |k| of an
-eddy-current mode of an unbounded Ohmic sheet, and Bean-limit flux fronts of a strip.
+eddy-current mode of an unbounded Ohmic sheet, and Bean-limit flux fronts of a strip; by
+tests/test_oracle_power_law_pins.py: the exact jc and e0 scalings of Eq. 3 with a lognormal jc
+map, the Bean strip with a non-uniform jc (|j| = local jc in the penetrated zones), and Eq. 12's
+multiplier as lambda times the smoothed field of the stray current; by
+tests/test_oracle_direct_sums.py: every multiplier against O(N^2) Fourier sums.
 """
 from __future__ import annotations
 
@@ -41,6 +45,7 @@ import math
 
 import numpy as np
 
+from . import _fft as dft
 from .waveform import Waveform
 
 OK, NOCONV = 0, 3
@@ -93,12 +98,12 @@ class FilmProblem:
     @staticmethod
     def apply(mult: np.ndarray, f: np.ndarray) -> np.ndarray:
         """Re F^-1[mult F f] with the discrete Fourier transform."""
-        return np.real(np.fft.ifft2(mult * np.fft.fft2(f)))
+        return np.real(dft.ifft2(mult * dft.fft2(f)))
 
     def gradient(self, g: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
         """Gaussian-smoothed spectral gradient of g (Section 2.2)."""
-        gh = np.fft.fft2(g)
-        return np.real(np.fft.ifft2(self.Dx * gh)), np.real(np.fft.ifft2(self.Dy * gh))
+        gh = dft.fft2(g)
+        return np.real(dft.ifft2(self.Dx * gh)), np.real(dft.ifft2(self.Dy * gh))
 
     def sheet_current(self, g: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
         """Eq. 2: j_x = d_y g, j_y = -d_x g."""
@@ -116,7 +121,7 @@ class FilmProblem:
         """Eq. 4 / Eq. 9: h_z_dot = -(d_x e_y - d_y e_x) on the conductor, 0 elsewhere."""
         jx, jy = self.sheet_current(g)
         ex, ey = self.electric_field(jx, jy)
-        curl = np.real(np.fft.ifft2(self.Dx * np.fft.fft2(ey) - self.Dy * np.fft.fft2(ex)))
+        curl = np.real(dft.ifft2(self.Dx * dft.fft2(ey) - self.Dy * dft.fft2(ex)))
         return np.where(self.conductor, -curl, 0.0)
 
     # ---- the right-hand side -------------------------------------------------------------

@@ -50,6 +50,9 @@ def test_film_operators_equal_direct_fourier_sums():
     kab = lambda kx, ky: np.sqrt(kx * kx + ky * ky)
     k1 = lambda kx, ky, a, b: np.where(kab(kx, ky) > 0, 2 / np.maximum(kab(kx, ky), 1e-300), 0)
     np.testing.assert_allclose(p.apply(p.K1, f), _direct_2d(f, Lx, Ly, k1), atol=1e-12)
+    # Eq. 12's multiplier lambda (|k|/2) exp(-|k|^2 sigma^2/2), lambda = 0.7 (Section 2.2)
+    np.testing.assert_allclose(p.apply(p.K2, f), _direct_2d(f, Lx, Ly, lambda kx, ky, a, b:
+                                                           0.7 * kab(kx, ky) / 2 * G(kx, ky)), atol=1e-12)
     np.testing.assert_allclose(p.hz(0.4, f) - WF.he(0.4),
                                _direct_2d(f, Lx, Ly, lambda kx, ky, a, b: kab(kx, ky) / 2), atol=1e-12)
 
