@@ -91,7 +91,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -141,22 +141,6 @@ def _oracle_problem(wl):
     wf = Waveform(*wl.he_knots) if wl.he_knots else Waveform(sin_amp=wl.he_sin[0], sin_period=wl.he_sin[1])
     return FilmProblem(wl.nx, wl.ny, wl.Lx, wl.Ly, wl.mask, n=wl.n, rho_out=wl.rho_out, waveform=wf,
                        iter_tol=wl.iter_tol, iter_max=wl.iter_max, lam=wl.lam)
-
-
-def cpu_sample(wl, iters: int, budget_s: float):
-    """Time forced-iteration oracle right-hand sides of the workload until `budget_s` is used."""
-    import workloads as W
-    o = _oracle_problem(wl)
-    g = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=3, amplitude=0.4)
-    n = 0
-    t0 = time.perf_counter()
-    while True:
-        o.rhs(0.05 + 1e-4 * n, g, None, max(1, iters))
-        n += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or n >= 50:
-            break
-    return n / el, n, el
 
 
 def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128):
@@ -329,6 +313,102 @@ def full_ramp_leg(native, W, torch, precision: int):
             "oracle_seconds": cpu_sec}
 
 
+def golden_ramp_leg(native, W, torch, which: str):
+    """Full ramp of a stated workload on the GPU (FP32 transforms, FP64 state), free running from
+    a zero state, timed end to end (mf_run_ramp with its readouts), with its relative L2 errors
+    against the FP64 oracle's stored ramp (tests/golden/, written by make_ramp_goldens.py)."""
+    import numpy as np
+    wl = W.rect_film_2048(precision=1) if which == "film" else W.cube_bulk(128, precision=1)
+    path = os.path.join(ROOT, "tests", "golden", f"ramp_{wl.name}.npz")
+    if not os.path.exists(path):
+        return {"workload": wl.name, "skipped": "no stored oracle ramp"}
+    ref = np.load(path)
+    meta = json.load(open(path.replace(".npz", ".json")))
+    p = native.from_workload(wl)
+    t_out = ref["t_out"]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    m, fields = p.mf_run_ramp(t_out, want_fields=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - w0
+    info = p.mf_get_info()
+    stride = meta["field_stride"]
+    errs = []
+    for tf, fref in zip(ref["t_fields"], ref["fields"]):
+        k = int(np.argmin(np.abs(t_out - tf)))
+        f = fields[k].cpu().numpy()
+        if wl.dim == 2:
+            f = f.reshape(wl.ny, wl.nx)[::stride, ::stride]
+        else:
+            lo, hi = wl.nx // 4 - 4, 3 * wl.nx // 4 + 4
+            f = f.reshape(3, wl.nz, wl.ny, wl.nx)[:, lo:hi:stride, lo:hi:stride, lo:hi:stride]
+        errs.append(float(np.linalg.norm(f - fref) / np.linalg.norm(fref)))
+    mref = ref["m"].reshape(len(t_out), -1)
+    m_err = float(np.linalg.norm(m - mref) / np.linalg.norm(mref))
+    return {"workload": wl.name, "transforms": "f32", "t_end": float(t_out[-1]), "seconds": sec,
+            "accepted_steps": info["n_accepted"], "rejected_steps": info["n_rejected"],
+            "rhs_evals": info["n_rhs"], "outside_iterations": info["n_iters"],
+            "rel_err_m": m_err, "rel_err_field": max(errs), "field": meta["field"],
+            "tolerance": 2e-4, "oracle_seconds": meta["oracle_seconds"],
+            "oracle_fft_workers": meta["fft_workers"],
+            "oracle_steps": meta["attempts"]}
+
+
+def fp64_leg(native, W, torch, steps: int = 5, warmup: int = 3):
+    """Secondary line: the same film and start with FP64 transforms (the plain FP64 solver),
+    timed like the main line, and the precision form's speed-up over it."""
+    wl = W.rect_film_2048(precision=0)
+    p = native.from_workload(wl)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    p.mf_set_state(T_START, torch.as_tensor(g0, device="cuda"), h=H_START)
+    p.mf_advance(1.0, max_attempts=warmup)
+    torch.cuda.synchronize()
+    i0 = p.mf_get_info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(p.stream)
+    p.mf_advance(1.0, max_attempts=steps)
+    e1.record(p.stream)
+    torch.cuda.synchronize()
+    i1 = p.mf_get_info()
+    sec = e0.elapsed_time(e1) / 1000.0
+    n_rhs, n_it = i1["n_rhs"] - i0["n_rhs"], i1["n_iters"] - i0["n_iters"]
+    M = wl.nx * wl.ny * 8.0
+    alg = rhs_bytes(n_rhs, n_it, M)
+    peak, kind = hbm_peak()
+    return {"workload": wl.name, "transforms": "f64", "value": n_rhs / sec, "unit": UNIT,
+            "steps": i1["n_attempts"] - i0["n_attempts"], "rhs_evals": n_rhs,
+            "mean_outside_iterations": n_it / max(n_rhs, 1),
+            "ms_per_round_trip": 1000.0 * sec / (2 * n_rhs + 2 * n_it),
+            "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
+                         "bytes_model": "(19 + 14 I) M per RHS, M = 2048^2 x 8 B"}}
+
+
+def cufft_leg(torch, n: int = 2048, reps: int = 50):
+    """Reference point only (the library never calls it): cuFFT round trips
+    irfft2(M * rfft2(x)) of an n x n real field through torch.fft, in FP32 and FP64, CUDA-event
+    timed after warm-up."""
+    out = {"grid": [n, n], "note": "torch.fft (cuFFT) round trip with a pointwise multiplier; "
+                                   "timed beside the library as a reference point only"}
+    for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        x = torch.randn(n, n, device="cuda", dtype=dt)
+        mult = torch.rand(n, n // 2 + 1, device="cuda", dtype=dt)
+
+        def rt():
+            return torch.fft.irfft2(torch.fft.rfft2(x) * mult, s=(n, n))
+        for _ in range(5):
+            rt()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            rt()
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"ms_per_round_trip_{name}"] = e0.elapsed_time(e1) / reps
+    return out
+
+
 def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
     """Whole-job figures of a multi-rank run: the slowest rank's timed seconds, the evaluations of
     all ranks and the sum of the ranks' end-to-end rates (the replicas run side by side).
@@ -344,24 +424,274 @@ def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
 
 
 def cores_used() -> int:
-    # numpy's FFT (pocketfft) and elementwise kernels run on one thread
-    return 1
+    """Host threads of the oracle's transforms (scipy.fft workers); its elementwise steps run on
+    one thread."""
+    from oracle import _fft
+    return _fft.workers()
+
+
+T_START = 0.05          # the timed steps start mid-cycle from a seeded critical-state film
+H_START = 2e-5
+
+
+def bench_config(wl) -> dict:
+    """The workload both arms time (identical in the two JSON lines)."""
+    return {"workload": wl.name, "grid": [wl.nx, wl.ny], "film_cells": [wl.nx // 2, wl.ny // 4],
+            "n": wl.n, "he": "0.8 sin(2 pi t)", "rtol": wl.rtol, "atol": wl.atol,
+            "iter_tol": wl.iter_tol, "outside_iteration": "converged, warm-started (Section 2.2)",
+            "start": f"seeded critical-state film at t = {T_START}, h = {H_START}, after the warm-up",
+            "l2": "working set > L2 (no flush)"}
+
+
+class _Enough(Exception):
+    pass
+
+
+def oracle_rhs_sample(warmup: int, count: int = 0, budget_s: float = 0.0):
+    """The FP64 oracle on the benchmark workload and start state: its own Bogacki-Shampine
+    integrator and warm-started outside iteration from t = T_START, `warmup` right-hand sides
+    untimed, then `count` timed right-hand sides (or as many as `budget_s` seconds allow, at least
+    two).  Returns (RHS per second, timed RHS, seconds, mean outside iterations, t reached)."""
+    import numpy as np
+    import workloads as W
+    from oracle.bs23 import BS23
+    wl = W.rect_film_2048(precision=0)
+    o = _oracle_problem(wl)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    marks = {}
+    iters = []
+
+    def rhs(t, y, seg, force):
+        if len(iters) == warmup:
+            marks["t0"] = time.perf_counter()
+        r = o.rhs(t, y, seg, force)
+        iters.append(r[1])
+        n = len(iters) - warmup
+        if n > 0:
+            marks["t1"] = time.perf_counter()
+            if (count and n >= count) or (budget_s and n >= 2 and marks["t1"] - marks["t0"] > budget_s):
+                raise _Enough
+        return r
+
+    s = BS23(rhs, o.wf, rtol=wl.rtol, atol=wl.atol, h0=H_START, on_accept=o.accept,
+             on_attempt=o.begin_attempt)
+    s.start(T_START, g0, 1.0)
+    try:
+        s.advance(1.0)
+    except _Enough:
+        pass
+    n = len(iters) - warmup
+    el = marks["t1"] - marks["t0"]
+    return n / el, n, el, float(np.mean(iters[warmup:])), s.t
 
 
 def run_reference(args):
+    """The oracle (FP64, CPU) on the same workload and start state as the GPU arm, W right-hand
+    sides of warm-up, then exactly K timed right-hand sides (one step of this arm = one
+    right-hand side, the unit of the metric)."""
     import workloads as W
-    wl = W.rect_film_2048(precision=1)
-    iters = 5
-    rate, n, el = cpu_sample(wl, iters, budget_s=20.0)      # a bounded sample: about 20 s
+    wl = W.rect_film_2048(precision=0)
+    W_, K = max(1, args.warmup), max(1, args.steps)
+    rate, n, el, mean_it, t_reached = oracle_rhs_sample(W_, count=K)
+    cores = cores_used()
+    sample = (f"{K} right-hand sides (after {W_} of warm-up) of the oracle's own BS23 run of the "
+              f"{wl.nx}x{wl.ny} film from the GPU arm's start state: converged warm-started outside "
+              f"iterations, mean {mean_it:.1f}; transforms on {cores} threads, elementwise steps on one")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / n,
+            "steps": K, "warmup": W_, "ms_per_step": 1000.0 * el / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny], "n": wl.n,
-                       "iterations_per_rhs": iters},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-                             "sample": f"{n} right-hand sides of the {wl.nx}x{wl.ny} film with "
-                                       f"{iters} forced outside iterations each"},
+            "data": "synthetic", "config": bench_config(wl),
+            "run": {"step": "one right-hand side", "mean_outside_iterations": mean_it,
+                    "t_reached": t_reached},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def golden_ramp_leg(native, W, torch, which: str):
+    """Full ramp of a stated workload on the GPU (FP32 transforms, FP64 state), free running from
+    a zero state, timed end to end (mf_run_ramp with its readouts), with its relative L2 errors
+    against the FP64 oracle's stored ramp (tests/golden/, written by make_ramp_goldens.py)."""
+    import numpy as np
+    wl = W.rect_film_2048(precision=1) if which == "film" else W.cube_bulk(128, precision=1)
+    path = os.path.join(ROOT, "tests", "golden", f"ramp_{wl.name}.npz")
+    if not os.path.exists(path):
+        return {"workload": wl.name, "skipped": "no stored oracle ramp"}
+    ref = np.load(path)
+    meta = json.load(open(path.replace(".npz", ".json")))
+    p = native.from_workload(wl)
+    t_out = ref["t_out"]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    m, fields = p.mf_run_ramp(t_out, want_fields=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - w0
+    info = p.mf_get_info()
+    stride = meta["field_stride"]
+    errs = []
+    for tf, fref in zip(ref["t_fields"], ref["fields"]):
+        k = int(np.argmin(np.abs(t_out - tf)))
+        f = fields[k].cpu().numpy()
+        if wl.dim == 2:
+            f = f.reshape(wl.ny, wl.nx)[::stride, ::stride]
+        else:
+            lo, hi = wl.nx // 4 - 4, 3 * wl.nx // 4 + 4
+            f = f.reshape(3, wl.nz, wl.ny, wl.nx)[:, lo:hi:stride, lo:hi:stride, lo:hi:stride]
+        errs.append(float(np.linalg.norm(f - fref) / np.linalg.norm(fref)))
+    mref = ref["m"].reshape(len(t_out), -1)
+    m_err = float(np.linalg.norm(m - mref) / np.linalg.norm(mref))
+    return {"workload": wl.name, "transforms": "f32", "t_end": float(t_out[-1]), "seconds": sec,
+            "accepted_steps": info["n_accepted"], "rejected_steps": info["n_rejected"],
+            "rhs_evals": info["n_rhs"], "outside_iterations": info["n_iters"],
+            "rel_err_m": m_err, "rel_err_field": max(errs), "field": meta["field"],
+            "tolerance": 2e-4, "oracle_seconds": meta["oracle_seconds"],
+            "oracle_fft_workers": meta["fft_workers"],
+            "oracle_steps": meta["attempts"]}
+
+
+def fp64_leg(native, W, torch, steps: int = 5, warmup: int = 3):
+    """Secondary line: the same film and start with FP64 transforms (the plain FP64 solver),
+    timed like the main line, and the precision form's speed-up over it."""
+    wl = W.rect_film_2048(precision=0)
+    p = native.from_workload(wl)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    p.mf_set_state(T_START, torch.as_tensor(g0, device="cuda"), h=H_START)
+    p.mf_advance(1.0, max_attempts=warmup)
+    torch.cuda.synchronize()
+    i0 = p.mf_get_info()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(p.stream)
+    p.mf_advance(1.0, max_attempts=steps)
+    e1.record(p.stream)
+    torch.cuda.synchronize()
+    i1 = p.mf_get_info()
+    sec = e0.elapsed_time(e1) / 1000.0
+    n_rhs, n_it = i1["n_rhs"] - i0["n_rhs"], i1["n_iters"] - i0["n_iters"]
+    M = wl.nx * wl.ny * 8.0
+    alg = rhs_bytes(n_rhs, n_it, M)
+    peak, kind = hbm_peak()
+    return {"workload": wl.name, "transforms": "f64", "value": n_rhs / sec, "unit": UNIT,
+            "steps": i1["n_attempts"] - i0["n_attempts"], "rhs_evals": n_rhs,
+            "mean_outside_iterations": n_it / max(n_rhs, 1),
+            "ms_per_round_trip": 1000.0 * sec / (2 * n_rhs + 2 * n_it),
+            "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
+                         "bytes_model": "(19 + 14 I) M per RHS, M = 2048^2 x 8 B"}}
+
+
+def cufft_leg(torch, n: int = 2048, reps: int = 50):
+    """Reference point only (the library never calls it): cuFFT round trips
+    irfft2(M * rfft2(x)) of an n x n real field through torch.fft, in FP32 and FP64, CUDA-event
+    timed after warm-up."""
+    out = {"grid": [n, n], "note": "torch.fft (cuFFT) round trip with a pointwise multiplier; "
+                                   "timed beside the library as a reference point only"}
+    for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        x = torch.randn(n, n, device="cuda", dtype=dt)
+        mult = torch.rand(n, n // 2 + 1, device="cuda", dtype=dt)
+
+        def rt():
+            return torch.fft.irfft2(torch.fft.rfft2(x) * mult, s=(n, n))
+        for _ in range(5):
+            rt()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            rt()
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"ms_per_round_trip_{name}"] = e0.elapsed_time(e1) / reps
+    return out
+
+
+def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's timed seconds, the evaluations of
+    all ranks and the sum of the ranks' end-to-end rates (the replicas run side by side).
+    `dist` is torch.distributed with an initialised process group, or None for one rank."""
+    if dist is None:
+        return sec, float(n_rhs), e2e_rate
+    import torch
+    mx = torch.tensor([sec], device=device, dtype=torch.float64)
+    sm = torch.tensor([float(n_rhs), e2e_rate], device=device, dtype=torch.float64)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0]), float(sm[1])
+
+
+def cores_used() -> int:
+    """Host threads of the oracle's transforms (scipy.fft workers); its elementwise steps run on
+    one thread."""
+    from oracle import _fft
+    return _fft.workers()
+
+
+T_START = 0.05          # the timed steps start mid-cycle from a seeded critical-state film
+H_START = 2e-5
+
+
+def bench_config(wl) -> dict:
+    """The workload both arms time (identical in the two JSON lines)."""
+    return {"workload": wl.name, "grid": [wl.nx, wl.ny], "film_cells": [wl.nx // 2, wl.ny // 4],
+            "n": wl.n, "he": "0.8 sin(2 pi t)", "rtol": wl.rtol, "atol": wl.atol,
+            "iter_tol": wl.iter_tol, "outside_iteration": "converged, warm-started (Section 2.2)",
+            "start": f"seeded critical-state film at t = {T_START}, h = {H_START}, after the warm-up",
+            "l2": "working set > L2 (no flush)"}
+
+
+class _Enough(Exception):
+    pass
+
+
+def run_reference(args):
+    """The oracle (FP64, CPU) on the same workload and start state as the GPU arm: its own
+    Bogacki-Shampine integrator and warm-started outside iteration, W right-hand sides of
+    warm-up, then exactly K timed right-hand sides (one step of this arm = one right-hand side,
+    the unit of the metric)."""
+    import numpy as np
+    import workloads as W
+    from oracle.bs23 import BS23
+    wl = W.rect_film_2048(precision=0)
+    o = _oracle_problem(wl)
+    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
+    W_, K = max(1, args.warmup), max(1, args.steps)
+    marks = {}
+    iters = []
+
+    def rhs(t, y, seg, force):
+        n = len(iters)
+        if n == W_:
+            marks["t0"] = time.perf_counter()
+        r = o.rhs(t, y, seg, force)
+        iters.append(r[1])
+        if len(iters) == W_ + K:
+            marks["t1"] = time.perf_counter()
+            raise _Enough
+        return r
+
+    s = BS23(rhs, o.wf, rtol=wl.rtol, atol=wl.atol, h0=H_START, on_accept=o.accept,
+             on_attempt=o.begin_attempt)
+    s.start(T_START, g0, 1.0)
+    try:
+        s.advance(1.0)
+    except _Enough:
+        pass
+    el = marks["t1"] - marks["t0"]
+    rate = K / el
+    timed_iters = iters[W_:]
+    cores = cores_used()
+    sample = (f"{K} right-hand sides (after {W_} of warm-up) of the oracle's own BS23 run of the "
+              f"{wl.nx}x{wl.ny} film from the GPU arm's start state: converged warm-started outside "
+              f"iterations, mean {np.mean(timed_iters):.1f}; transforms on {cores} threads, "
+              f"elementwise steps on one")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W_, "ms_per_step": 1000.0 * el / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(wl),
+            "run": {"step": "one right-hand side", "mean_outside_iterations": float(np.mean(timed_iters)),
+                    "t_reached": s.t},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -375,7 +705,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the bulk and full-ramp legs")
     ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
-    ap.add_argument("--only", choices=["batch", "adjoint"], help="run one secondary leg alone")
+    ap.add_argument("--only", choices=["batch", "adjoint", "ramps", "fp64", "cufft"],
+                    help="run one secondary leg alone")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max-side", type=int, default=512)
     args = ap.parse_args()
@@ -405,6 +736,18 @@ def main():
         if rank == 0:
             print(json.dumps(adjoint_leg(native, W, torch)))
         return
+    if args.only == "ramps":
+        if rank == 0:
+            print(json.dumps([golden_ramp_leg(native, W, torch, w) for w in ("film", "cube")]))
+        return
+    if args.only == "fp64":
+        if rank == 0:
+            print(json.dumps(fp64_leg(native, W, torch)))
+        return
+    if args.only == "cufft":
+        if rank == 0:
+            print(json.dumps(cufft_leg(torch)))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -420,8 +763,7 @@ def main():
     # start of the outside iteration
     g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100 + rank, amplitude=0.3)
     y = torch.as_tensor(g0, device="cuda")
-    t_start = 0.05
-    p.mf_set_state(t_start, y, h=2e-5)
+    p.mf_set_state(T_START, y, h=H_START)
     p.mf_advance(1.0, max_attempts=max(1, args.warmup))
     torch.cuda.synchronize()
 
@@ -480,30 +822,42 @@ def main():
         traffic_ratio = profiled_traffic("film_kernel_f32", wl.name)
         cpu = None
         if not args.no_cpu:
-            rate, n, el = cpu_sample(wl, max(1, round(mean_it)), budget_s=15.0)
+            rate, n, el, mit, _ = oracle_rhs_sample(2, budget_s=15.0)
             cpu = {"value": rate, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-                   "sample": f"{n} FP64 right-hand sides of the {wl.nx}x{wl.ny} film with "
-                             f"{max(1, round(mean_it))} forced outside iterations each "
-                             f"({el:.1f} s on the host)"}
+                   "sample": f"{n} right-hand sides (after 2 of warm-up) of the FP64 oracle's own "
+                             f"BS23 run of the {wl.nx}x{wl.ny} film from this line's start state, "
+                             f"converged outside iterations (mean {mit:.1f}); {el:.1f} s; transforms "
+                             f"on {cores_used()} threads, elementwise steps on one"}
         info = p.mf_get_info()
         bulk = bulk_leg(native, W, torch) if not args.no_extra else None
         bulk_256 = bulk_leg(native, W, torch, n_grid=256) if not args.no_extra else None
         tune = autotune_leg(native, W, torch, args.grid) if not args.no_extra else None
         adj = adjoint_leg(native, W, torch) if not args.no_extra else None
         batch = batch_leg(native, W, torch) if not args.no_extra else None
-        ramps = [full_ramp_leg(native, W, torch, prec) for prec in (0, 1)] if not args.no_extra else None
+        ramps = None
+        if not args.no_extra:
+            ramps = [full_ramp_leg(native, W, torch, prec) for prec in (0, 1)]
+            ramps += [golden_ramp_leg(native, W, torch, w) for w in ("film", "cube")]
+        f64 = fp64_leg(native, W, torch) if not args.no_extra else None
+        if f64 is not None:
+            f64["speedup_of_f32_form"] = (n_rhs / sec) / f64["value"]
+        cufft = cufft_leg(torch) if not args.no_extra else None
+        if cufft is not None:
+            cufft["library_ms_per_round_trip_f32"] = 1000.0 * sec / (2 * n_rhs + 2 * n_it)
+            if f64 is not None:
+                cufft["library_ms_per_round_trip_f64"] = f64["ms_per_round_trip"]
         line = {
             "metric": METRIC, "value": rhs_all / sec_all, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny], "film_cells": [wl.nx // 2, wl.ny // 4],
-                       "n": wl.n, "he": "0.8 sin(2 pi t)", "state": "f64", "transforms": "f32",
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "working set > L2 (no flush)", "t_start": t_start, "t_end": t_now,
-                       "step_attempts": n_att, "rhs_evals": n_rhs,
-                       "mean_outside_iterations": mean_it, "grid_ctas": info["grid"],
-                       "threads": info["threads"]},
+            "config": bench_config(wl),
+            "run": {"step": "one BS23 step attempt (3-4 right-hand sides, error norm, control)",
+                    "state": "f64", "transforms": "f32",
+                    "parallelism": "replicas" if world > 1 else "single", "t_end": t_now,
+                    "step_attempts": n_att, "rhs_evals": n_rhs, "mean_outside_iterations": mean_it,
+                    "grid_ctas": info["grid"], "threads": info["threads"],
+                    "ms_per_round_trip": 1000.0 * sec / (2 * n_rhs + 2 * n_it)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": None if traffic_ratio is None else traffic_ratio * alg,
@@ -524,6 +878,8 @@ def main():
             "adjoint": adj,
             "batch": batch,
             "full_ramp": ramps,
+            "fp64": f64,
+            "cufft": cufft,
         }
         print(json.dumps(line))
     if dist:

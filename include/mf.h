@@ -95,7 +95,7 @@ typedef struct {
   long long workspace_used;
 } mf_info;
 
-enum { MF_READ_HZ = 0, MF_READ_MOMENT = 1, MF_READ_J = 2 };
+enum { MF_READ_HZ = 0, MF_READ_MOMENT = 1, MF_READ_J = 2, MF_READ_E = 3 };
 
 /* Defaults: dim 2, n 19, jc = e0 = 1, rho_out 1, lambda 0.7, iter_tol 2e-4, iter_max 1000,
    precision 0, rtol = atol = 1e-6, h_min 1e-12, he_dir (0,0,1). */
@@ -124,6 +124,14 @@ mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, in
    force_iters outside iterations (for lock-step comparison with another implementation). */
 mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double* d_ydot,
                     int force_iters, int* iters_out);
+
+/* Time limit of one grid-barrier wait inside the persistent launches (seconds; <= 0 restores
+   the default of 4 s).  A launch whose wait runs out raises an abort flag that every CTA polls,
+   so all CTAs leave promptly and the call returns MF_ERR_BARRIER; the problem stays usable (call
+   mf_reset_warm before relying on the warm start again).  This bounds every wait so that a CTA
+   that never arrives (which a cooperative launch rules out) cannot hang the GPU.  The paper has
+   no counterpart: it is part of the library's failure detection. */
+mf_status mf_set_barrier_timeout(mf_problem* pb, double seconds);
 
 /* Forget the warm starts (previous call and previous time step): the next right-hand side
    starts from h_e_dot on free space. */
@@ -186,8 +194,11 @@ mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_
 /* Readout of the current state: MF_READ_HZ (film: h_z = h_e + F^-1[(|k|/2) F g], end of
    Section 2.1; nx*ny values), MF_READ_MOMENT (film: m_z = integral of g; bulk:
    m = 1/2 integral of r x j over the conductor; 1 or 3 values), MF_READ_J (bulk:
-   j = curl h, 3 fields).  d_out is device memory, except for MF_READ_MOMENT where it is host
-   memory. */
+   j = curl h, 3 fields), MF_READ_E (the electric field e = rho(|j|) j of Eq. 3 (film, j from
+   Eq. 2; 2 fields e_x, e_y) or Eq. 13 (bulk; 3 fields), Ohm law rho_out j outside the
+   superconductor, with the Gaussian-smoothed derivatives of Section 2.2 / Section 3.1; the
+   transform precision's power law).  d_out is device memory (float64, fields back to back),
+   except for MF_READ_MOMENT where it is host memory. */
 mf_status mf_readout(mf_problem* pb, int what, double* out);
 
 /* Same readouts of an arbitrary device state vector d_y at time t. */
@@ -295,10 +306,12 @@ void mf_destroy(mf_problem* pb);
    Limits: p->nx, p->ny <= 256, otherwise MF_ERR_WORKSPACE with a message in err.
    d_y, d_ydot: device float64, nx*ny values; force_iters as in mf_rhs_ex; *iters_out (may be
    NULL) gets the outside iterations; err (may be NULL) gets err_len bytes of message.
-   The first call on a device looks up the array's device address with that device current;
-   make that first call before any stream capture.  Every call shares the array and leaves
-   its contents behind; each call restarts the outside iteration cold (no warm start), and
-   calls whose GPU work overlaps in time race on the array.  The call synchronises `stream`. */
+   The first call on a device looks up the array's device address with that device current.
+   Every call copies its tables, mask, jc map and state into the array from the host and
+   synchronises `stream` several times (and once more to read the status back), so no call can
+   be captured into a CUDA graph.  Every call shares the array and leaves its contents behind;
+   each call restarts the outside iteration cold (no warm start), and calls whose GPU work
+   overlaps in time race on the array. */
 mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const double* d_y, double* d_ydot,
                               int force_iters, void* stream, int* iters_out, char* err,
                               size_t err_len);

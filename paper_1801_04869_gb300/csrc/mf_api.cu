@@ -260,6 +260,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   d.sigma = p->sigma > 0 ? p->sigma : std::sqrt(s2);   // Section 2.2 / Section 3.2 choice
   d.n = p->n; d.e0 = p->e0; d.jc = p->jc; d.rho_out = p->rho_out; d.lam = p->lambda;
   d.iter_tol = p->iter_tol; d.iter_max = p->iter_max;
+  d.barrier_ns = BARRIER_LIMIT_NS;
   d.rtol = p->rtol; d.atol = p->atol; d.h_min = p->h_min;
   d.he_knots = p->he_knots; d.he_sin_amp = p->he_sin_amp; d.he_sin_period = p->he_sin_period;
   for (int i = 0; i < 3; ++i) d.he_dir[i] = p->he_dir[i];
@@ -402,6 +403,15 @@ mf_status mf_rhs_ex(mf_problem* pb, double t, int seg, const double* d_y, double
 
 mf_status mf_rhs(mf_problem* pb, double t, const double* d_y, double* d_ydot, int* iters_out) {
   return mf_rhs_ex(pb, t, -2, d_y, d_ydot, 0, iters_out);
+}
+
+mf_status mf_set_barrier_timeout(mf_problem* pb, double seconds) {
+  if (!pb || !(seconds == seconds) || seconds > 3600.0) return MF_ERR_ARG;
+  pb->d.barrier_ns = seconds <= 0.0 ? BARRIER_LIMIT_NS
+                                    : std::max(1ull, (unsigned long long)(seconds * 1e9));
+  MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.dev, &pb->d, sizeof(Desc), cudaMemcpyHostToDevice, pb->stream));
+  MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
+  return MF_OK;
 }
 
 mf_status mf_reset_warm(mf_problem* pb) {
@@ -703,6 +713,7 @@ mf_status mf_readout_of(mf_problem* pb, int what, double t, const double* d_y, d
   }
   if (what == MF_READ_HZ && pb->d.dim == 2) { a.mode = MODE_HZ; a.out = out; return launch(pb, a); }
   if (what == MF_READ_J && pb->d.dim == 3) { a.mode = MODE_J; a.out = out; return launch(pb, a); }
+  if (what == MF_READ_E) { a.mode = MODE_E; a.out = out; return launch(pb, a); }
   pb->err = "readout not available for this dimension";
   return MF_ERR_ARG;
 }

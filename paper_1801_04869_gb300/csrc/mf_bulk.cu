@@ -74,7 +74,7 @@ struct Bulk {
     nblocks = gridDim.x;
   }
 
-  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed); }
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed, d.barrier_ns); }
 
   __device__ BulkPtrs<T> ptrs() const {
     return BulkPtrs<T>{mask, jcmap, hd, ncell, nx, ny, d.Lx, d.Ly, d.Lz, d.dx, d.dy, d.dz};
@@ -401,6 +401,19 @@ struct BStoreJ : EpiBase<T> {              // readout of j = curl h (FP64)
 };
 
 template <typename T>
+struct BStoreE : EpiBase<T> {              // readout of e = rho(|j|) j (Eq. 13 / Ohm law, FP64)
+  BulkPtrs<T> P;
+  T n, e0, jc, rho_out;
+  double* out;
+  __device__ void operator()(long long i, const T* in, T*) {
+    const int m = __ldg(&P.mask[i]);
+    const T jcl = P.jcmap ? __ldg(&P.jcmap[i]) : jc;
+    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
+    out[i] = rho * in[0]; out[P.ncell + i] = rho * in[1]; out[2 * P.ncell + i] = rho * in[2];
+  }
+};
+
+template <typename T>
 struct BMoment : EpiBase<T> {              // m = 1/2 sum dV r x j over the conductor, component `comp`
   BulkPtrs<T> P;
   int comp;
@@ -531,13 +544,17 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(const Desc* __restrict__ dg
                            nullptr, nullptr, nullptr);
     status = r.status == ST_OK && r.nonfinite ? ST_NONFINITE : r.status;
     if (leader) { st->last_iters = r.iters; st->last_r = r.r; st->n_rhs += 1; st->n_iters += r.iters; }
-  } else if (a.mode == MODE_J || a.mode == MODE_MOMENT) {
+  } else if (a.mode == MODE_J || a.mode == MODE_E || a.mode == MODE_MOMENT) {
     StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
     { BStage<T> e; e.P = B.ptrs(); e.in = in; B.xpass<0, 3>(e, -1); }
     bool ok = B.sync(201) && B.yzy(OP3_CURL, 202);
     if (ok) {
       if (a.mode == MODE_J) {
         BStoreJ<T> e; e.P = B.ptrs(); e.out = a.out;
+        B.xpass<3, 0>(e, -1);
+      } else if (a.mode == MODE_E) {
+        BStoreE<T> e; e.P = B.ptrs(); e.out = a.out;
+        e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
         B.xpass<3, 0>(e, -1);
       } else {
         for (int c = 0; c < 3 && ok; ++c) {

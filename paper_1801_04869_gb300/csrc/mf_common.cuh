@@ -169,6 +169,7 @@ struct Desc {
   int rows_per_item;             // 2D row pass / 3D x pass rows per work item (even)
   int zs_per_item;               // 3D y pass z-lines per work item
   int grid;                      // CTAs of the persistent launch
+  unsigned long long barrier_ns; // time limit of one grid-barrier wait (ns)
   const struct Desc* dev;        // device copy of this descriptor (what the kernels read)
 };
 
@@ -191,15 +192,17 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
 
-constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // 4 s per barrier
+constexpr unsigned long long BARRIER_LIMIT_NS = 4000000000ull;   // default: 4 s per barrier
 
 // Returns false when the launch must stop (abort raised).  `passed` counts the barriers this
 // CTA has passed in the launch (shared memory, written by thread 0 only, zero at launch).
 // Arrival is a fire-and-forget release add after the CTA barrier; the wait polls the same word
-// with acquire loads.
+// with acquire loads.  A wait longer than `limit_ns` raises the abort flag.
 __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks, int where,
-                                          unsigned long long* passed) {
+                                          unsigned long long* passed,
+                                          unsigned long long limit_ns = BARRIER_LIMIT_NS) {
   __shared__ int s_ok;
+  const unsigned long long lim = limit_ns ? limit_ns : BARRIER_LIMIT_NS;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned long long target = (*passed + 1) * nblocks;
@@ -212,7 +215,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int nblocks,
       do {
         __nanosleep(nap);
         if (nap < 128) nap <<= 1;
-        if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
+        if (globaltimer_ns() - t0 > lim) {
           atomicOr(&gb->count, BARRIER_ABORT);
           atomicExch(&gb->where, where);
           v |= BARRIER_ABORT;
@@ -323,15 +326,15 @@ __device__ __forceinline__ double reduce_partials(const double* partials, int ma
 // launch arguments of the persistent kernels
 // ------------------------------------------------------------------------------------------
 enum Mode { MODE_RHS = 0, MODE_ADVANCE = 1, MODE_HZ = 2, MODE_SETUP = 3, MODE_MOMENT = 4,
-            MODE_J = 5 };
+            MODE_J = 5, MODE_E = 6 };
 
 struct KernelArgs {
   int mode;
-  double t;                   // MODE_RHS / MODE_HZ / MODE_J: time
+  double t;                   // MODE_RHS / MODE_HZ / MODE_J / MODE_E: time
   double t_target;            // MODE_ADVANCE
   long long max_attempts;     // MODE_ADVANCE
   const double* y_in;         // MODE_RHS / MODE_HZ / MODE_MOMENT / MODE_J input (FP64)
-  double* out;                // MODE_RHS: derivative; MODE_HZ: h_z; MODE_J: j; MODE_MOMENT
+  double* out;                // MODE_RHS: derivative; MODE_HZ: h_z; MODE_J: j; MODE_E: e; MODE_MOMENT
   int force_iters;            // > 0: run exactly this many outside iterations
   int seg;                    // waveform segment for MODE_RHS (-2: from t)
 };

@@ -77,7 +77,7 @@ struct Film {
     nblocks = nblk;
   }
 
-  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed); }
+  __device__ bool sync(int where) { return grid_sync(d.gb, nblocks, where, &sh.bar_passed, d.barrier_ns); }
 
   __device__ FilmPtrs<T> ptrs() const { return FilmPtrs<T>{mask, jcmap, hd, u, q1, q2, nx}; }
 
@@ -475,6 +475,32 @@ struct EpiFinal : EpiBase<T> {
   }
 };
 
+// e readout (FP64, 2 fields): e = rho(|j|) j with j = (g_y, -g_x) (Eq. 2, Eq. 3), Ohm law
+// rho_out j on free space and filled holes
+template <typename T>
+struct EpiStoreE : EpiBase<T> {
+  FilmPtrs<T> P;
+  T n, e0, jc, rho_out;
+  double* dst;
+  long long ncell;
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
+    const uchar4 m = ldmask4(P.mask + i);
+    V4<T> jcl;
+    if (P.jcmap) jcl = ldg4(P.jcmap + i);
+    else jcl = V4<T>{{jc, jc, jc, jc}};
+    V4<double> ex, ey;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T jx = in[1].v[q], jy = -in[0].v[q];
+      const T rho = resistivity<T>(jx * jx + jy * jy, jcl.v[q], mask_at(m, q), n, e0, rho_out);
+      ex.v[q] = (double)(rho * jx);
+      ey.v[q] = (double)(rho * jy);
+    }
+    st4(dst + i, ex);
+    st4(dst + ncell + i, ey);
+  }
+};
+
 // magnetization: sum over D of g (times dx dy on the host side)
 template <typename T>
 struct EpiMoment : EpiBase<T> {
@@ -679,6 +705,17 @@ __device__ __forceinline__ void film_main(const Desc& d, const KernelArgs& a, in
       if (F.sync(31)) {
         EpiStoreHz<T> es; es.P = F.ptrs(); es.dst = a.out; es.he = he_value(d, a.t);
         F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
+      } else status = ST_BARRIER;
+    } else status = ST_BARRIER;
+  } else if (a.mode == MODE_E) {
+    EpiStage<T> e; e.P = F.ptrs(); e.in = StageIn{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
+    F.rows<0, 1>(F.rb1, nullptr, F.Sa, e, -1);
+    if (F.sync(50)) {
+      F.cols(F.Sa, 1, F.Sa, 2, OP_GRAD);
+      if (F.sync(51)) {
+        EpiStoreE<T> es; es.P = F.ptrs(); es.dst = a.out; es.ncell = F.ncell;
+        es.n = (T)d.n; es.e0 = (T)d.e0; es.jc = (T)d.jc; es.rho_out = (T)d.rho_out;
+        F.rows<2, 0>(F.rb2, F.Sa, nullptr, es, -1);
       } else status = ST_BARRIER;
     } else status = ST_BARRIER;
   } else if (a.mode == MODE_MOMENT) {

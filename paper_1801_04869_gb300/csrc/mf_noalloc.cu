@@ -12,7 +12,10 @@
 //
 // Rules of use (also stated in include/mf.h):
 //   * the first call on a device looks up the array's device address (cudaGetSymbolAddress)
-//     with that device current; make that first call before any stream capture;
+//     with that device current;
+//   * every call copies the tables, mask, jc map, state and descriptor into the array and
+//     synchronises `stream` several times (host-side staging and the status read-back), so a
+//     call can never be part of a stream capture;
 //   * all calls share the array and it keeps the last call's contents, so calls whose GPU
 //     work overlaps (two streams, two host threads, two devices sharing nothing is fine) race;
 //   * each call starts the outside iteration cold (no warm start is kept between calls).
@@ -107,6 +110,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   Desc d;
   std::memset(&d, 0, sizeof(d));
   d.dim = 2; d.nx = nx; d.ny = ny; d.nz = 1; d.precision = precision;
+  d.barrier_ns = BARRIER_LIMIT_NS;
   int l = 0; while ((1 << l) < nx) ++l; d.lgx = l;
   l = 0; while ((1 << l) < ny) ++l; d.lgy = l;
   d.Lx = p->Lx; d.Ly = p->Ly;

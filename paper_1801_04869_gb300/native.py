@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmf.so")
 
 MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_NOCONV, MF_ERR_NONFINITE = 0, 1, 2, 3, 4
 MF_ERR_STEP_UNDERFLOW, MF_ERR_WORKSPACE, MF_ERR_BARRIER = 5, 6, 7
-MF_READ_HZ, MF_READ_MOMENT, MF_READ_J = 0, 1, 2
+MF_READ_HZ, MF_READ_MOMENT, MF_READ_J, MF_READ_E = 0, 1, 2, 3
 STATUS_NAMES = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_NOCONV",
                 4: "MF_ERR_NONFINITE", 5: "MF_ERR_STEP_UNDERFLOW", 6: "MF_ERR_WORKSPACE",
                 7: "MF_ERR_BARRIER"}
@@ -30,7 +30,7 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
            "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp",
            "mf_film_solve_gradient_work_bytes", "mf_film_solve_gradient", "mf_set_jc_map",
-           "mf_set_knot_values"]
+           "mf_set_knot_values", "mf_set_barrier_timeout"]
 
 
 class mf_params(ctypes.Structure):
@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "mf_rhs": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, ip]),
         "mf_rhs_ex": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int, vp, vp, ctypes.c_int, ip]),
         "mf_reset_warm": (ctypes.c_int, [vp]),
+        "mf_set_barrier_timeout": (ctypes.c_int, [vp, ctypes.c_double]),
         "mf_set_state": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, vp]),
         "mf_get_state": (ctypes.c_int, [vp, dp, dp, vp]),
         "mf_advance": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_longlong]),
@@ -216,6 +217,10 @@ class Problem:
 
     def mf_reset_warm(self):
         self._check(self.lib.mf_reset_warm(self.h))
+
+    def mf_set_barrier_timeout(self, seconds: float):
+        """Time limit of one grid-barrier wait (<= 0: the default 4 s)."""
+        self._check(self.lib.mf_set_barrier_timeout(self.h, float(seconds)))
 
     def mf_set_state(self, t: float, y=None, h: float = 0.0):
         self._check(self.lib.mf_set_state(self.h, t, h, _dptr(y)))

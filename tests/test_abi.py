@@ -39,6 +39,15 @@ def test_struct_layouts_match_header(lib):
     assert p.n == 19.0 and p.lambda_ == 0.7 and p.iter_tol == 2e-4 and p.he_dir[2] == 1.0
 
 
+def test_readout_enum_matches_header():
+    from paper_1801_04869_gb300 import native
+    src = open(os.path.join(ROOT, "include", "mf.h")).read()
+    enum = re.search(r"enum \{ (MF_READ_[^}]*)\}", src).group(1)
+    vals = dict((k.strip(), int(v)) for k, v in (x.split("=") for x in enum.split(",")))
+    assert vals == {"MF_READ_HZ": native.MF_READ_HZ, "MF_READ_MOMENT": native.MF_READ_MOMENT,
+                    "MF_READ_J": native.MF_READ_J, "MF_READ_E": native.MF_READ_E}
+
+
 def test_workspace_query_and_argument_checks(lib):
     import numpy as np
     from paper_1801_04869_gb300 import native
@@ -77,6 +86,7 @@ def test_null_and_invalid_arguments_are_refused_without_a_gpu(lib):
     assert lib.mf_film_solve_gradient_work_bytes(None, 4) == 0
     assert lib.mf_set_jc_map(None, None) == native.MF_ERR_ARG
     assert lib.mf_set_knot_values(None, None) == native.MF_ERR_ARG
+    assert lib.mf_set_barrier_timeout(None, 1.0) == native.MF_ERR_ARG
     assert lib.mf_film_solve_gradient(None, 1, 1, None, None, None, None, None, 0, None, None,
                                       None) == native.MF_ERR_ARG
     one = (ctypes.c_int * 1)(64)

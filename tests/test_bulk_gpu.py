@@ -49,6 +49,20 @@ def test_current_readout_round_trip(dims, precision):
                                atol=1e-13 if precision == 0 else 1e-7)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_electric_field_readout(precision):
+    """e = rho(|j|) j (Eq. 13) with j = curl h, Ohm law outside: MF_READ_E against the oracle."""
+    wl = bulk_workload(32, 32, 32, precision=precision, ax=0.5, ay=0.4, az=0.3)
+    wl.jc_map = W.jc_map_lognormal((32, 32, 32), seed=19)
+    h = W.bulk_state(wl.mask, (wl.Lx, wl.Ly, wl.Lz), seed=20, h0=0.3, depth=0.3)
+    o = oracle_of(wl)
+    p = native.from_workload(wl)
+    out = torch.zeros((3, 32, 32, 32), dtype=torch.float64, device="cuda")
+    p.mf_readout(native.MF_READ_E, out=out, t=0.1, y=dev(h))
+    err = rel_l2(out.cpu().numpy(), o.electric_field(o.current(h)))
+    assert err < (TOL64 if precision == 0 else TOL32), err
+
+
 def _rhs_pair(wl, h, times, force=None, tol=TOL64):
     o = oracle_of(wl)
     p = native.from_workload(wl)

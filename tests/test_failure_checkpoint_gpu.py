@@ -31,6 +31,41 @@ def _nan_film(**kw):
     return wl, g
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_barrier_wait_that_runs_out_returns_a_status(dim):
+    """A grid-barrier time limit of 1 ns makes the first CTA to reach a barrier give up before
+    the others arrive: the launch raises its abort flag, every CTA leaves, and the call returns
+    MF_ERR_BARRIER (a bounded wait that returns, not a fault).  With the default limit restored
+    the same problem computes the oracle's right-hand side."""
+    from helpers import oracle_of
+    if dim == 2:
+        wl = film_workload(128, 128, precision=0, ax=1.0, ay=1.0)
+        y0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=62, amplitude=0.4)
+    else:
+        m = W.bulk_mask(32, 32, 32, 1.0, 1.0, 1.0, "box", ax=0.5, ay=0.5, az=0.5)
+        wl = W.Workload("cube32", 3, 32, 32, 32, 1.0, 1.0, 1.0, m, n=25.0, rho_out=5.0, precision=0,
+                        t0=0.0, t1=1.0, he_knots=((0.0, 1.0), (0.0, 0.5)), iter_tol=1e-4)
+        y0 = W.bulk_state(m, (1.0, 1.0, 1.0), seed=63)
+    p = native.from_workload(wl)
+    assert p.mf_get_info()["grid"] > 1
+    y = dev(y0)
+    out = torch.zeros_like(y)
+    p.mf_set_barrier_timeout(1e-9)
+    with pytest.raises(native.MFError) as e:
+        p.mf_rhs(0.2, y, out, force_iters=3)
+    assert e.value.status == native.MF_ERR_BARRIER
+    with pytest.raises(native.MFError) as e:
+        p.mf_advance(0.5, max_attempts=2)
+    assert e.value.status == native.MF_ERR_BARRIER
+    p.mf_set_barrier_timeout(0.0)                       # back to the default limit
+    p.mf_reset_warm()
+    it, st = p.mf_rhs(0.2, y, out, force_iters=3, allow_noconv=True)
+    ref, it_o, _ = oracle_of(wl).rhs(0.2, y0, None, 3)
+    assert it == it_o == 3
+    err = np.linalg.norm(out.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 1e-9, err
+
+
 def test_nan_state_is_rejected_until_step_underflow():
     """The outside iteration cannot converge on a NaN state: every attempt is rejected (outcome
     2) and halves h, until h < h_min ends the run with MF_ERR_STEP_UNDERFLOW.  The state is

@@ -45,6 +45,27 @@ def test_hz_readout_round_trip(nx, ny, precision):
     assert m[0] == pytest.approx(o.magnetization(g), rel=1e-12)
 
 
+@pytest.mark.parametrize("case", ["square_n19", "disk_hole_jc_map"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_electric_field_readout(case, precision):
+    """e = rho(|j|) j (Eq. 3) with j = (g_y, -g_x) (Eq. 2), Ohm law outside the film: the
+    MF_READ_E readout against the oracle's electric field."""
+    if case == "square_n19":
+        wl = film_workload(128, 128, precision=precision, ax=1.0, ay=1.0)
+    else:
+        wl = film_workload(256, 64, L=(4.0, 1.0), shape="disk", radius=0.8, hole=(0.3, 0.1, 0.25),
+                           n=30.0, rho_out=5.0, precision=precision)
+        wl.jc_map = W.jc_map_lognormal((64, 256), seed=9)
+    g = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=31, amplitude=0.8)
+    o = oracle_of(wl)
+    p = gpu_of(wl)
+    out = torch.zeros((2, wl.ny, wl.nx), dtype=torch.float64, device="cuda")
+    p.mf_readout(native.MF_READ_E, out=out, t=0.3, y=dev(g))
+    ex, ey = o.electric_field(*o.sheet_current(g))
+    err = rel_l2(out.cpu().numpy(), np.stack([ex, ey]))
+    assert err < (TOL64 if precision == 0 else TOL32), err
+
+
 def _rhs_pair(wl, g, times, force=None, precision_tol=TOL64):
     o = oracle_of(wl)
     p = gpu_of(wl)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import rel_l2
+from helpers import film_workload, oracle_of, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -63,3 +63,26 @@ def test_noalloc_fp32_and_size_limit():
     yb = torch.zeros((512, 512), dtype=torch.float64, device="cuda")
     st, _, msg = native.mf_film_rhs_noalloc(pb, 0.1, yb, torch.zeros_like(yb))
     assert st == native.MF_ERR_WORKSPACE and "exceeds the static scratch limit" in msg
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noalloc_nonsquare_grid_with_jc_map(precision):
+    """A 256 x 128 grid (non-square tables), a lognormal jc map (converted to the transform
+    precision inside the static array) and more than 32 knots of h_e: two calls in a row, each
+    against the regular entry point and the FP64 oracle."""
+    kt = np.linspace(0.0, 1.0, 40)
+    wl = film_workload(256, 128, L=(4.0, 2.0), shape="disk", radius=1.5, precision=precision,
+                       n=30.0, he_knots=(tuple(kt), tuple(0.5 * kt ** 1.5)))
+    wl.jc_map = W.jc_map_lognormal((128, 256), seed=34)
+    p = native.from_workload(wl)
+    tol = TOL64 if precision == 0 else 2e-4
+    for t, seed in ((0.33, 35), (0.71, 36)):
+        g = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=seed, amplitude=0.6)
+        y = torch.as_tensor(g, device="cuda")
+        out = torch.full_like(y, np.nan)
+        st, it, msg = native.mf_film_rhs_noalloc(p, t, y, out, force_iters=4)
+        ref, it_ref, st_ref = _regular(wl, t, g, 4)
+        assert st == st_ref == native.MF_OK and it == it_ref == 4, msg
+        assert rel_l2(out.cpu().numpy(), ref) < (TOL64 if precision == 0 else 1e-6)
+        want, _, _ = oracle_of(wl).rhs(t, g, None, 4)
+        assert rel_l2(out.cpu().numpy(), want) < tol
