@@ -13,7 +13,10 @@ and handles a failed outside iteration by letting the step control shrink the st
   err = max_i |E_i| / (atol + rtol max(|y_n,i|, |y_{n+1},i|)),  accept if err <= 1.
 
 Step control (a standard choice; the paper states none):
-  accept: h <- h min(5, max(0.2, 0.9 err^(-1/3))), capped at 1x right after a rejection
+  accept: h <- h min(5, max(0.2, 0.9 err^(-1/3))), capped at 1x right after a rejection; after
+          a step that was shortened to end on a knot or output time, h <- h_prop min(1, fac)
+          with h_prop the proposal before the shortening (a step shortened to a sliver, e.g. an
+          output time one ulp before a knot, must not collapse the next step)
   reject: h <- h max(0.2, 0.9 err^(-1/3));  non-converged stage (k1 included): h <- h/2, and
   a non-converged k1 is evaluated again on the next attempt (its warm start has advanced)
   h < h_min stops with STEP_UNDERFLOW.
@@ -85,6 +88,7 @@ class BS23:
             self.on_attempt()
         t, y = self.t, self.y
         t_lim = min(t_target, self.wf.next_knot(t))
+        h_prop = self.h
         if forced is None:
             h = self.h
             clipped = t + 1.1 * h >= t_lim
@@ -133,7 +137,9 @@ class BS23:
             fac = 5.0 if err == 0.0 else min(5.0, max(0.2, 0.9 * err ** (-1.0 / 3.0)))
             if self.failed:
                 fac = min(fac, 1.0)
-            self.h = h * fac
+            # a step shortened to end on a knot or output time says nothing about longer steps:
+            # the next one starts from the proposal it replaced (never above it)
+            self.h = h_prop * min(fac, 1.0) if (clipped and h < h_prop) else h * fac
             self.failed = False
         elif outcome == REJECT_ERR:
             self.h = h * max(0.2, 0.9 * err ** (-1.0 / 3.0))

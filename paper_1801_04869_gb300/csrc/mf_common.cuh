@@ -111,7 +111,8 @@ struct SolverState {
   long long log_count;
   double last_r;                 // last convergence residual
   double last_err;
-  double pad[3];
+  double q11;                    // (2D) sum over free space of q1 = F^-1[K1 F(out)] (set-up)
+  double pad[2];
 };
 
 // Barrier state of one launch (zeroed before every launch).  `count` is a monotonic arrival
@@ -320,6 +321,24 @@ __device__ __forceinline__ double reduce_partials(const double* partials, int ma
   const double s = red[0];
   __syncthreads();
   return s;
+}
+
+// Sums of two slots over i < n (fixed order, as reduce_partials), read in one pass by the first
+// warp; red[0], red[1] receive them.  The caller combines them in thread 0 and broadcasts.
+__device__ __forceinline__ void reduce_partials2(const double* partials, int max_items, int slot_a,
+                                                 int slot_b, int n, double* red) {
+  if (threadIdx.x < 32) {
+    const double* pa = partials + (size_t)slot_a * max_items;
+    const double* pb = partials + (size_t)slot_b * max_items;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) {
+      a += __ldcg(pa + i);
+      b += __ldcg(pb + i);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) { red[0] = a; red[1] = b; }
+  }
 }
 
 // ------------------------------------------------------------------------------------------

@@ -9,13 +9,15 @@
 //   P5  x pass: h_dot_in on the conductor, warm h_dot on free space, sum for A (Eq. 10)
 //   loop (Eqs. 11-12):
 //   P6  y pass: 2/|k|
-//   P7  x pass: u = raw - A q1, sum over free space (C), forward of mask_out u
-//   P8  residual r = mean_out |u - C| (stop test, Section 2.3), in the same phase as
-//   P9  y pass: lambda (|k|/2) G (discarded when the stop test ends the loop)
-//   P10 x pass: h_dot_out <- h_dot_out - A - (w - C q2), sum for the next A, forward
-//   end: g_dot = (u - C) on the conductor, 0 on free space (FP64)
-// The constants A and C are applied through the precomputed fields q1 = F^-1[K1 F(out)] and
-// q2 = F^-1[K2 F(out)], which is exact by linearity and saves one pass per iteration.
+//   P7  x pass: g_dot = raw - A q1 - C, residual sum over free space of |g_dot| (the stop
+//       test of Section 2.3), forward of mask_out g_dot
+//   P9  y pass: lambda (|k|/2) G (only when the stop test did not end the loop)
+//   P10 x pass: h_dot_out <- h_dot_out - A - w, sums for the next A and C, forward
+//   end: g_dot on the conductor, 0 on free space (FP64)
+// The shift A (Eq. 10) is applied lazily through q1 = F^-1[K1 F(out)] (exact by linearity).
+// The centring constant C (Eq. 11), the mean over free space of raw - A q1, is known before
+// the x pass that forms g_dot: K1 is real and even, so sum_out F^-1[K1 F h] = <q1, h>, and
+// C = (<q1, h> - A sum_out q1) / n_out with <q1, h> summed where h is written (P5, P10).
 #pragma once
 #include "mf_rhs_common.cuh"
 
@@ -263,24 +265,56 @@ struct Film {
     if constexpr (NOUT > 0) rows_forward_scatter<T, NOUT>(X, Y, Sout + y0, nspec, ny, npair, lgpair, lgx, twx);
     epi_io.acc = epi.acc;
     epi_io.accmax = epi.accmax;
+    epi_io.acc2 = epi.acc2;
   }
 
-  // rows pass with an optional per-item reduction into partials slot `slot`
+  // rows pass with optional per-item reductions into partials slots `slot` (acc or accmax)
+  // and `slot2` (acc2)
   template <int NIN, int NOUT, class Epi>
-  __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot) {
+  __device__ void rows(int rb, const C2<T>* Sin, C2<T>* Sout, Epi& epi, int slot, int slot2 = -1) {
     const int nitems = ny / rb;
     for (int it = vb; it < nitems; it += (int)nblocks) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
+      epi.acc2 = 0.0;
       row_item<NIN, NOUT>(it * rb, rb, Sin, Sout, epi);
       if (slot >= 0) {
         const double v = epi.is_max ? block_max(epi.accmax, sh.red) : block_sum(epi.acc, sh.red);
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
       }
+      if (slot2 >= 0) {
+        const double v = block_sum(epi.acc2, sh.red);
+        if (threadIdx.x == 0) d.partials[(size_t)slot2 * d.max_items + it] = v;
+      }
     }
   }
   __device__ double total(int slot, int rb, bool is_max = false) {
     return reduce_partials(d.partials, d.max_items, slot, ny / rb, is_max, sh.red);
+  }
+  // Eq. 10 and Eq. 11 constants from the sums of h (slot 0) and q1 h (slot 5) of the pass that
+  // wrote h: A = (sum h - N h_e_dot) / n_out, C = (<q1, h> - A sum_out q1) / n_out; computed once
+  // by thread 0 and broadcast (the double-precision division runs at a low rate on this part)
+  __device__ void shifts(int rb, double N, double hed, double nout, double& A, double& C) {
+    reduce_partials2(d.partials, d.max_items, 0, 5, ny / rb, sh.red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double a = (sh.red[0] - N * hed) / nout;
+      sh.red[2] = a;
+      sh.red[3] = (sh.red[1] - a * sh.q11) / nout;
+    }
+    __syncthreads();
+    A = sh.red[2];
+    C = sh.red[3];
+    __syncthreads();
+  }
+  // mean over free space of the residual sum in slot 2 (broadcast like shifts)
+  __device__ double mean_out(int slot, int rb, double nout) {
+    const double s = reduce_partials(d.partials, d.max_items, slot, ny / rb, false, sh.red);
+    if (threadIdx.x == 0) sh.red[2] = s / nout;
+    __syncthreads();
+    const double r = sh.red[2];
+    __syncthreads();
+    return r;
   }
 };
 
@@ -319,12 +353,18 @@ struct EpiOut : EpiBase<T> {
   }
 };
 
-// store a real field (set-up)
+// store a real field (set-up); sum of it over free space
 template <typename T>
 struct EpiStoreT : EpiBase<T> {
   FilmPtrs<T> P;
   T* dst;
-  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) { st4(dst + i, in[0]); }
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
+    st4(dst + i, in[0]);
+    const uchar4 m = ldmask4(P.mask + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (mask_at(m, q) == 0) this->acc += (double)in[0].v[q];
+  }
 };
 // h_z readout (FP64)
 template <typename T>
@@ -372,79 +412,66 @@ struct EpiInit : EpiBase<T, T> {
     const uchar4 m = ldmask4(P.mask + i);
     V4<T> w;
     if (warm) w = ld4(wsrc + i);
+    const V4<T> q1 = ldg4(P.q1 + i);
     V4<T> h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (mask_at(m, q) != 0) h.v[q] = in[0].v[q];             // h_dot_in on the conductor
       else h.v[q] = warm ? w.v[q] - A_prev : hed;             // warm start (Section 2.2)
       this->acc += h.v[q];
+      this->acc2 += q1.v[q] * h.v[q];                         // <q1, h> for C
     }
     st4(P.hd + i, h);
     out[0] = h;
   }
 };
 
-// P7: u = raw - A q1; sum over free space; forward of mask_out u
+// P7: g_dot = raw - A q1 - C (Eq. 11), stored; residual sum over free space of |g_dot|
+// (Section 2.3); forward of mask_out g_dot (the input of Eq. 12)
 template <typename T>
 struct EpiU : EpiBase<T, T> {
   FilmPtrs<T> P;
-  T A;
+  T A, C;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     const V4<T> q1 = ldg4(P.q1 + i);
     V4<T> v;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      v.v[q] = in[0].v[q] - A * q1.v[q];
+      v.v[q] = (in[0].v[q] - A * q1.v[q]) - C;
       const bool o = mask_at(m, q) == 0;
-      if (o) this->acc += v.v[q];
+      if (o) this->acc += fabs(v.v[q]);
       out[0].v[q] = o ? v.v[q] : (T)0;
     }
     st4(P.u + i, v);
   }
 };
 
-// P8: residual sum over free space of |u - C|
-template <typename T>
-struct EpiResid : EpiBase<T, T> {
-  FilmPtrs<T> P;
-  T C;
-  __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
-    const uchar4 m = ldmask4(P.mask + i);
-    const V4<T> u = ld4(P.u + i);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (mask_at(m, q) == 0) this->acc += fabs(u.v[q] - C);
-  }
-};
-
-// P10: h_dot update on free space (Eq. 12), sum over D, forward
+// P10: h_dot update on free space (Eq. 12: w is the transform of mask_out g_dot), sums over D
+// of h (for A) and of q1 h (for C), forward
 template <typename T>
 struct EpiUpdate : EpiBase<T, T> {
   FilmPtrs<T> P;
-  T A, C;
+  T A;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     V4<T> h = ld4(P.hd + i);
-    const V4<T> q2 = ldg4(P.q2 + i);
+    const V4<T> q1 = ldg4(P.q1 + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (mask_at(m, q) == 0) {
-        const T w = in[0].v[q] - C * q2.v[q];
-        h.v[q] = (h.v[q] - A) - w;
-      }
+      if (mask_at(m, q) == 0) h.v[q] = (h.v[q] - A) - in[0].v[q];
       this->acc += h.v[q];
+      this->acc2 += q1.v[q] * h.v[q];
     }
     st4(P.hd + i, h);
     out[0] = h;
   }
 };
 
-// finalize: g_dot = (u - C) on the conductor; optional BS23 error contribution
+// finalize: g_dot (stored by P7) on the conductor; optional BS23 error contribution
 template <typename T>
 struct EpiFinal : EpiBase<T> {
   FilmPtrs<T> P;
-  double C;
   double* kout;
   // error estimate (stage 4 of a step): E = h (e1 k1 + e2 k2 + e3 k3 + e4 k4)
   bool err;
@@ -455,7 +482,7 @@ struct EpiFinal : EpiBase<T> {
     const V4<T> u = ld4(P.u + i);
     V4<double> g;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g.v[q] = mask_at(m, q) != 0 ? (double)u.v[q] - C : 0.0;
+    for (int q = 0; q < 4; ++q) g.v[q] = mask_at(m, q) != 0 ? (double)u.v[q] : 0.0;
     st4(kout + i, g);
     if (err) {
       const V4<double> a1 = ld4(k1 + i), a2 = ld4(k2 + i), a3 = ld4(k3 + i), yy = ld4(y + i), yn = ld4(ynew + i);
@@ -557,11 +584,13 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     e.warm = com || F.sh.warm_valid != 0;
     e.wsrc = com ? hdc : hdw;
     e.A_prev = (T)(com ? F.sh.A_com : F.sh.A_prev); e.hed = (T)hed;
-    F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                              // P5
+    F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0, 5);                           // P5
   }
   if (!F.sync(5)) { res.status = ST_BARRIER; return res; }
-  double A = have_out ? (F.total(0, F.rb1) - N * hed) / nout : 0.0;    // Eq. 10
-  double C = 0.0, r = 0.0;
+  // Eq. 10: A; Eq. 11: C = (<q1, h> - A sum_out q1) / n_out (K1 is real and even)
+  double A = 0.0, C = 0.0;
+  if (have_out) F.shifts(F.rb1, N, hed, nout, A, C);
+  double r = 0.0;
   const bool forced = force_iters > 0;
   const bool fixed = d.iter_tol <= 0.0;
   int itmax = forced ? force_iters : d.iter_max;
@@ -571,42 +600,23 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
     F.cols(F.Sa, 1, F.Sa, 1, OP_K1);                                    // P6
     if (!F.sync(6)) { res.status = ST_BARRIER; return res; }
     {
-      EpiU<T> e; e.P = F.ptrs(); e.A = (T)A;
-      F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 1);                            // P7
+      EpiU<T> e; e.P = F.ptrs(); e.A = (T)A; e.C = (T)C;
+      F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 2);                            // P7
     }
     if (!F.sync(7)) { res.status = ST_BARRIER; return res; }
-    if (!have_out) { C = 0.0; r = 0.0; break; }
-    C = F.total(1, F.rb1) / nout;                                       // Eq. 11
-    {
-      // P9 (K2 column items, the longer ones, first) and P8 (residual, row items) share one
-      // phase and one item space
-      EpiResid<T> e; e.P = F.ptrs(); e.C = (T)C;
-      const int nl9 = F.col_lines(1);
-      const int n8 = F.ny / F.rb1, n9 = (F.nkx + nl9 - 1) / nl9;
-      for (int it = F.vb; it < n8 + n9; it += (int)F.nblocks) {
-        if (it < n9) {
-          const int kx0 = it * nl9;
-          F.col_item(kx0, kx0 + nl9 <= F.nkx ? nl9 : F.nkx - kx0, F.Sb, 1, F.Sb, 1, OP_K2);
-        } else {
-          const int r8 = it - n9;
-          e.acc = 0.0;
-          F.template row_item<0, 0>(r8 * F.rb1, F.rb1, nullptr, nullptr, e);
-          const double v = block_sum(e.acc, F.sh.red);
-          if (threadIdx.x == 0) d.partials[(size_t)2 * d.max_items + r8] = v;
-        }
-      }
-    }
-    if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
-    r = F.total(2, F.rb1) / nout;
+    if (!have_out) { r = 0.0; break; }
+    r = F.mean_out(2, F.rb1, nout);                                     // Section 2.3
     const bool last = (i == itmax - 1);
     const bool stop = (forced || fixed) ? last : (r < d.iter_tol || last);
     if (stop) break;
+    F.cols(F.Sb, 1, F.Sb, 1, OP_K2);                                    // P9 (Eq. 12)
+    if (!F.sync(8)) { res.status = ST_BARRIER; return res; }
     {
-      EpiUpdate<T> e; e.P = F.ptrs(); e.P.hd = hdw; e.A = (T)A; e.C = (T)C;
-      F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0);                            // P10
+      EpiUpdate<T> e; e.P = F.ptrs(); e.P.hd = hdw; e.A = (T)A;
+      F.rows<1, 1>(F.rb1, F.Sb, F.Sa, e, 0, 5);                         // P10
     }
     if (!F.sync(10)) { res.status = ST_BARRIER; return res; }
-    A = (F.total(0, F.rb1) - N * hed) / nout;                           // Eq. 10
+    F.shifts(F.rb1, N, hed, nout, A, C);                                // Eq. 10, Eq. 11
   }
   res.iters = i + 1;
   res.r = r;
@@ -620,7 +630,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
 
   // finalize
   {
-    EpiFinal<T> e; e.P = F.ptrs(); e.C = C; e.kout = kout; e.is_max = true;
+    EpiFinal<T> e; e.P = F.ptrs(); e.kout = kout; e.is_max = true;
     e.err = want_err; e.h = h_err; e.rtol = d.rtol; e.atol = d.atol;
     e.k1 = e_k1; e.k2 = e_k2; e.k3 = e_k3; e.y = e_y; e.ynew = e_ynew;
     F.rows<0, 0>(F.rb1, nullptr, nullptr, e, 3);
@@ -678,6 +688,7 @@ __device__ __forceinline__ void film_main(const Desc& d, const KernelArgs& a, in
     sh.hd_sel = st->hd_sel;
     sh.A_com = st->A_com;
     sh.attempt_first = 0;
+    sh.q11 = st->q11;
   }
   if (threadIdx.x == 0) new (objraw) Film<T>(d, sm, sh, vb, vn);
   __syncthreads();
@@ -694,8 +705,12 @@ __device__ __forceinline__ void film_main(const Desc& d, const KernelArgs& a, in
       F.cols(F.Sa, 1, F.Sa, 1, pass == 0 ? OP_K1 : OP_K2);
       if (!F.sync(21)) { status = ST_BARRIER; break; }
       EpiStoreT<T> es; es.P = F.ptrs(); es.dst = (T*)(pass == 0 ? d.q1 : d.q2);
-      F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, -1);
+      F.rows<1, 0>(F.rb1, F.Sa, nullptr, es, 4);
       if (!F.sync(22)) { status = ST_BARRIER; break; }
+      if (pass == 0) {
+        const double q11 = F.total(4, F.rb1);          // sum over free space of q1
+        if (leader) st->q11 = q11;
+      }
     }
   } else if (a.mode == MODE_HZ) {
     EpiStage<T> e; e.P = F.ptrs(); e.in = StageIn{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};

@@ -26,6 +26,7 @@ struct Shared {
   double A_prev;
   int com_valid, hd_sel;         // (2D) accepted-step initial approximation, see SolverState
   double A_com;
+  double q11;                    // (2D) sum over free space of q1 (from the solver state)
   int attempt_first;             // (2D) the next right-hand side is the first of a step attempt
   unsigned long long bar_passed;  // grid barriers passed in this launch (thread 0)
 };
@@ -70,6 +71,7 @@ __device__ __forceinline__ double he_next_knot(const Desc& d, double t) {
 template <typename T, typename Acc = double>
 struct EpiBase {
   Acc acc = 0, accmax = 0;
+  Acc acc2 = 0;                 // a second sum (rows() with a second slot)
   bool is_max = false;
 };
 
@@ -103,6 +105,7 @@ __device__ int bs23_advance(Rhs& R, const Desc& d, SolverState* st, const Kernel
     double last_r = 0.0, last_err = 0.0;
     while (t < a.t_target && att < a.max_attempts) {
       const double t_lim = fmin(a.t_target, he_next_knot(d, t));
+      const double h_prop = h;         // the controller's proposal before clipping
       const bool clipped = t + 1.1 * h >= t_lim;
       if (clipped) h = t_lim - t;
       R.on_attempt();                  // the attempt's first evaluation starts from the accepted step
@@ -168,7 +171,9 @@ __device__ int bs23_advance(Rhs& R, const Desc& d, SolverState* st, const Kernel
         k1_valid = knot_hit ? 0 : 1;
         double fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -1.0 / 3.0)));
         if (failed) fac = fmin(fac, 1.0);
-        h = h * fac;
+        // a step shortened to end on a knot or output time says nothing about longer steps:
+        // the next one starts from the proposal it replaced (never above it)
+        h = (clipped && h < h_prop) ? h_prop * fmin(fac, 1.0) : h * fac;
         failed = 0;
         ++n_acc;
         last_err = err;

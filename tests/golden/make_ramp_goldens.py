@@ -16,6 +16,7 @@ free-running ramps with these files at the precision form's tolerance (2e-4 rela
   python tests/golden/make_ramp_goldens.py <case> [--t-end T] [--n-out K]
 
 --t-end stops the ramp early (a segment [t0, T] of the stated ramp); the sidecar records it.
+The files are rewritten at every field snapshot, so an interrupted run leaves a shorter segment.
 """
 from __future__ import annotations
 
@@ -91,6 +92,27 @@ def main():
     s.start(t0, y0, wl.t1)           # first step as the library chooses it for the stated ramp
     ms, fields, t_fields = [], [], []
     w0 = time.time()
+    out = os.path.join(HERE, f"ramp_{wl.name}.npz")
+
+    def save(n_done: int, wall: float):
+        """Write what has been computed so far (the ramp up to output time n_done)."""
+        np.savez_compressed(out, t_out=t_out[:n_done], m=np.array(ms), t_fields=np.array(t_fields),
+                            fields=np.array(fields))
+        meta = {"workload": wl.name, "case": args.case, "t0": t0, "t_end": float(t_out[n_done - 1]),
+                "t_end_requested": args.t_end, "n_out": n_done, "field": "h_z" if wl.dim == 2 else "j",
+                "field_stride": FILM_STRIDE if wl.dim == 2 else CUBE_STRIDE,
+                "grid": [wl.nx, wl.ny, wl.nz], "n": wl.n, "rho_out": wl.rho_out,
+                "rtol": wl.rtol, "atol": wl.atol, "iter_tol": wl.iter_tol,
+                "attempts": len(s.log), "accepted": sum(1 for e in s.log if e.outcome == 1),
+                "rhs_evals": int(sum(sum(1 for i in e.iters if i >= 0) for e in s.log)),
+                "outside_iterations": int(sum(sum(i for i in e.iters if i > 0) for e in s.log)),
+                "oracle_seconds": wall, "fft_workers": _fft.workers(),
+                "made_by": "tests/golden/make_ramp_goldens.py (oracle/ only)"}
+        with open(out.replace(".npz", ".json"), "w") as f:
+            json.dump(meta, f, indent=1)
+        return meta
+
+    meta = None
     for k, t in enumerate(t_out):
         st = s.advance(float(t))
         if st != 0:
@@ -100,24 +122,9 @@ def main():
         if (k + 1) % snap_every == 0 or k == len(t_out) - 1:
             fields.append(f)
             t_fields.append(float(t))
+            meta = save(k + 1, time.time() - w0)     # a snapshot closes a stored segment
         acc = sum(1 for e in s.log if e.outcome == 1)
         print(f"t = {t:.4f}  steps {len(s.log)} ({acc} accepted)  {time.time() - w0:.0f} s", flush=True)
-    wall = time.time() - w0
-    out = os.path.join(HERE, f"ramp_{wl.name}.npz")
-    np.savez_compressed(out, t_out=t_out, m=np.array(ms), t_fields=np.array(t_fields),
-                        fields=np.array(fields))
-    meta = {"workload": wl.name, "case": args.case, "t0": t0, "t_end": args.t_end,
-            "n_out": args.n_out, "field": "h_z" if wl.dim == 2 else "j",
-            "field_stride": FILM_STRIDE if wl.dim == 2 else CUBE_STRIDE,
-            "grid": [wl.nx, wl.ny, wl.nz], "n": wl.n, "rho_out": wl.rho_out,
-            "rtol": wl.rtol, "atol": wl.atol, "iter_tol": wl.iter_tol,
-            "attempts": len(s.log), "accepted": sum(1 for e in s.log if e.outcome == 1),
-            "rhs_evals": int(sum(sum(1 for i in e.iters if i >= 0) for e in s.log)),
-            "outside_iterations": int(sum(sum(i for i in e.iters if i > 0) for e in s.log)),
-            "oracle_seconds": wall, "fft_workers": _fft.workers(),
-            "made_by": "tests/golden/make_ramp_goldens.py (oracle/ only)"}
-    with open(out.replace(".npz", ".json"), "w") as f:
-        json.dump(meta, f, indent=1)
     print(json.dumps(meta))
 
 

@@ -152,3 +152,18 @@ def test_ramp_fp64_lock_step_small_cube():
     # the first attempt after the knot recomputes k1 (h_e_dot jumps there)
     after = [e for e in log if e[0] == 0.5]
     assert after and after[0][4][0] >= 0
+
+
+def test_ramp_with_an_output_time_one_ulp_before_a_knot():
+    """Output times from numpy.linspace put 0.49999999999999994 one ulp before the knot at 0.5:
+    the sliver step to the knot is accepted and the next step starts from the step size the
+    sliver replaced (it once collapsed to 5 x 5.6e-17 and stopped with step underflow)."""
+    wl = bulk_workload(32, 32, 32, precision=1)
+    p = native.from_workload(wl)
+    t_out = np.linspace(0.05, 1.0, 20)
+    m, _ = p.mf_run_ramp(t_out)
+    info = p.mf_get_info()
+    assert info["t"] == 1.0 and info["n_noconv"] == 0
+    log = p.mf_get_log()
+    slivers = [e for e in log if e[3] == 1 and e[1] < 1e-12]
+    assert len(slivers) == 1 and slivers[0][2] == 0.5

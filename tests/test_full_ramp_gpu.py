@@ -1,0 +1,66 @@
+"""Full ramps of the stated workloads on the GPU against the FP64 oracle's stored ramps.
+
+* The 1024 x 512-cell rectangle in a 2048^2 grid (n = 30, h_e = 0.8 sin 2 pi t; Section 2.2
+  method), FP32 transforms with FP64 state: m_z at every output time and h_z (sampled on every
+  16th cell) at the snapshot times, over the stored segment of the cycle.
+* The cube of 64^3 cells in a 128^3 grid (n = 25, rho_out = 5, h_e,z ramped to 0.25 on [0, 0.5]
+  and held; Section 3.1 method), FP32 transforms with FP64 state: m at every output time and j
+  (sampled on every 4th cell of the cube and its rim) at the snapshot times.
+
+Both run free (the GPU's own adaptive steps and converged outside iterations) from a zero state
+and are gated at the precision form's 2e-4 relative L2.  The stored ramps are written by
+tests/golden/make_ramp_goldens.py, which calls only the oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1801_04869_gb300 import native  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL32 = 2e-4
+
+
+def _stored(wl):
+    path = os.path.join(HERE, "golden", f"ramp_{wl.name}.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle ramp for {wl.name}")
+    return np.load(path), json.load(open(path.replace(".npz", ".json")))
+
+
+def _sample(wl, f, stride):
+    if wl.dim == 2:
+        return f.reshape(wl.ny, wl.nx)[::stride, ::stride]
+    lo, hi = wl.nx // 4 - 4, 3 * wl.nx // 4 + 4
+    return f.reshape(3, wl.nz, wl.ny, wl.nx)[:, lo:hi:stride, lo:hi:stride, lo:hi:stride]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["rect_film_2048", "cube_128"])
+def test_free_running_ramp_matches_stored_oracle_ramp(which):
+    wl = W.rect_film_2048(precision=1) if which == "rect_film_2048" else W.cube_bulk(128, precision=1)
+    ref, meta = _stored(wl)
+    t_out = ref["t_out"]
+    assert len(t_out) >= 2 and meta["workload"] == wl.name
+    p = native.from_workload(wl)
+    m, fields = p.mf_run_ramp(t_out, want_fields=True)
+    info = p.mf_get_info()
+    assert info["n_noconv"] == 0 and abs(info["t"] - t_out[-1]) < 1e-12
+    mref = ref["m"].reshape(len(t_out), -1)
+    err_m = np.linalg.norm(m - mref) / np.linalg.norm(mref)
+    assert err_m < TOL32, err_m
+    for tf, fref in zip(ref["t_fields"], ref["fields"]):
+        k = int(np.argmin(np.abs(t_out - tf)))
+        f = _sample(wl, fields[k].cpu().numpy(), meta["field_stride"])
+        err = np.linalg.norm(f - fref) / np.linalg.norm(fref)
+        assert err < TOL32, (tf, err)

@@ -114,3 +114,25 @@ def test_failed_first_stage_is_retried_with_half_step():
     assert s.log[0].iters[0] >= 0 and s.log[1].iters[0] >= 0 and s.log[2].iters[0] >= 0
     assert s.log[1].h == pytest.approx(0.05) and s.log[2].h == pytest.approx(0.025)
     assert s.y[0] == pytest.approx(math.exp(-0.3), rel=1e-5)
+
+
+def test_sliver_step_before_a_knot_does_not_collapse_the_step_size():
+    # an output time one ulp before a knot (numpy's linspace gives 0.49999999999999994 for 0.5)
+    # leaves a step of 5.6e-17 to the knot; the step after it starts again from the proposal
+    # the sliver replaced instead of from 5 x 5.6e-17 (which is below h_min)
+    w = Waveform((0.0, 0.5, 1.0), (0.0, 0.25, 0.25))
+
+    def rhs(t, y, seg, force):
+        return -y + w.hedot(t, seg), 1, 0
+
+    s = BS23(rhs, w, rtol=1e-6, atol=1e-6)
+    s.start(0.0, np.array([0.0]), 1.0)
+    t_out = np.linspace(0.05, 1.0, 20)
+    assert t_out[9] < 0.5 and 0.5 - t_out[9] < 1e-15
+    for t in t_out:
+        assert s.advance(float(t)) == 0
+    assert s.t == 1.0
+    sliver = [e for e in s.log if e.outcome == ACCEPT and e.h < 1e-12]
+    assert len(sliver) == 1 and sliver[0].t_new == 0.5
+    after = s.log[s.log.index(sliver[0]) + 1]
+    assert after.h > 1e-4
