@@ -230,32 +230,56 @@ mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, doub
 mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const double* d_v,
                           double* d_gbar, double* d_jcbar, double* sbar);
 
-/* Gradient of a film solve.  The map: from the state d_g0 (device FP64, nx*ny), n_steps
-   Bogacki-Shampine steps with the given times and sizes (host t_steps[i], h_steps[i]; every step
-   inside one segment of the h_e knots, all accepted: y <- y + h (2/9 k1 + 1/3 k2 + 4/9 k3)),
-   each right-hand side with a cold-started outside iteration of exactly `iters` iterations; the
-   loss L = 1/2 dx dy sum (h_z(T) - target)^2 with h_z = h_e + F^-1[(|k|/2) F g] (end of Section
-   2.1) at T = t_steps[n-1] + h_steps[n-1] and d_target device FP64 (nx*ny).  Writes *loss (host),
-   dL/djc per cell to d_jcbar (device FP64, nx*ny; zero outside the superconductor) and dL/dv_k
-   for the knot values of h_e to knots_bar (host, he_knots entries).  The forward keeps every
-   step's state in d_work (device, at least mf_film_solve_gradient_work_bytes bytes); the reverse
-   sweep recomputes each step's stages from it and runs mf_film_rhs_vjp three times per step.
-   Runs on the problem's stream and waits; the solver's own state is untouched but its warm
-   start is cleared and its counters count these evaluations.  MF_ERR_ARG for a bulk problem, a
-   film without free space, a sinusoidal h_e or a step across a knot; MF_ERR_WORKSPACE for a
-   short work buffer.  The adjoint has no counterpart in the paper. */
+/* Vector-Jacobian product of one warm-started film right-hand side with a fixed outside
+   iteration count, as the integrator runs it (Section 2.2: each call starts from the previous
+   call's last free-space iterate).  Besides g, jc and h_e_dot the call has a fourth input, the
+   warm start (free-space h_dot), and a second output, its last iterate.  Given the state d_g,
+   the cotangent d_v of f and d_wbar_out of the last iterate (device FP64, nx*ny each; free-space
+   values used; NULL = 0), writes the cotangents of g (d_gbar), of the jc map (d_jcbar, zero
+   outside the superconductor), of the warm start (d_wbar_in, zero on the conductor; may be
+   NULL) and of h_e_dot (*sbar, host, may be NULL).  The power law is linearised as in
+   mf_film_rhs_vjp.  One persistent launch; waits; clears the warm start.  The adjoint has no
+   counterpart in the paper. */
+mf_status mf_film_rhs_vjp_warm(mf_problem* pb, int iters, const double* d_g, const double* d_v,
+                               const double* d_wbar_out, double* d_gbar, double* d_jcbar,
+                               double* d_wbar_in, double* sbar);
+
 /* Replace the per-cell critical current density (device FP64, nx*ny[*nz]) of a problem that was
    created with a jc map (MF_ERR_ARG otherwise), or the knot values of a piecewise-linear h_e
-   (host, he_knots entries; the knot times stay).  Both wait for the problem's stream; later
-   calls use the new values.  They let a gradient's parameters change without a new problem. */
+   (host, n_values entries, which must equal the problem's he_knots, else MF_ERR_ARG; the knot
+   times stay).  Both wait for the problem's stream; later calls use the new values.  They let a
+   gradient's parameters change without a new problem. */
 mf_status mf_set_jc_map(mf_problem* pb, const double* d_jc);
-mf_status mf_set_knot_values(mf_problem* pb, const double* h_values);
+mf_status mf_set_knot_values(mf_problem* pb, const double* h_values, int n_values);
 
-size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps);
-mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const double* t_steps,
-                                 const double* h_steps, const double* d_g0, const double* d_target,
-                                 void* d_work, size_t work_bytes, double* d_jcbar,
-                                 double* knots_bar, double* loss);
+/* Loss and gradient of a film solve with frozen decisions.  The map is the one the integrator
+   evaluates once its decisions are fixed: from the state d_g0 (device FP64, nx*ny), n_steps
+   Bogacki-Shampine steps with the given times and sizes (host t_steps[i], h_steps[i]; every step
+   inside one segment of the h_e knots, all accepted: y <- y + h (2/9 k1 + 1/3 k2 + 4/9 k3)), each
+   right-hand side (k1, k2, k3 of step i are calls 3i, 3i+1, 3i+2) running exactly iters[call]
+   outside iterations (host, 3 n_steps counts >= 1: e.g. those the Section 2.3 stop test chose
+   in a forward run) from the previous call's last iterate; the first call starts from d_warm0
+   (device FP64 free-space field) or, if NULL, cold from h_e_dot.  The loss is
+   L = 1/2 dx dy sum (h_z(T) - target)^2 with h_z = h_e + F^-1[(|k|/2) F g] (end of Section 2.1),
+   T = t_steps[n-1] + h_steps[n-1], d_target device FP64 (nx*ny).  Writes *loss (host) and, when
+   d_jcbar is not NULL, dL/djc per cell to d_jcbar (device FP64, nx*ny; zero outside the
+   superconductor), dL/dv_k for the n_knots knot values of h_e to knots_bar (host; n_knots must
+   equal he_knots) and, when d_warm0_bar is not NULL, dL/d(first warm start) (device FP64).
+   d_jcbar = knots_bar = d_warm0_bar = NULL computes the loss alone (forward only).  Memory: the
+   forward keeps a checkpoint (state and warm start) every ckpt_every steps in d_work (device, at
+   least mf_film_solve_gradient_work_bytes(pb, n_steps, ckpt_every) bytes); the reverse sweep
+   recomputes each segment's stage inputs from its checkpoint and runs mf_film_rhs_vjp_warm three
+   times per step, carrying the warm-start cotangent from call to call.  Runs on the problem's
+   stream and waits; the solver's state is untouched, its warm start is cleared and its counters
+   count these evaluations.  MF_ERR_ARG for a bulk problem, a film without free space, a
+   sinusoidal h_e, a step across a knot, a count below 1 or a knot-count mismatch;
+   MF_ERR_WORKSPACE for a short work buffer.  The adjoint has no counterpart in the paper. */
+size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps, int ckpt_every);
+mf_status mf_film_solve_gradient(mf_problem* pb, int n_steps, const double* t_steps,
+                                 const double* h_steps, const int* iters, int ckpt_every,
+                                 const double* d_g0, const double* d_warm0, const double* d_target,
+                                 void* d_work, size_t work_bytes, double* d_jcbar, double* knots_bar,
+                                 int n_knots, double* d_warm0_bar, double* loss);
 
 /* Checkpoints: everything a continuation reads — the integrator state and counters, the six
    FP64 state/derivative buffers (with the first-same-as-last derivative), the outside

@@ -37,7 +37,10 @@ namespace mf {
 // transposed outside iteration of a film (csrc/mf_film_adjoint.cu)
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
                                 double* sbar, int iters, const double* g, double* gbar,
-                                double* jcbar, cudaStream_t s);
+                                double* jcbar, const double* wbar_out, double* wbar_in,
+                                cudaStream_t s);
+cudaError_t adj_warm_io(int precision, long long n, int load, const uint8_t* mask, void* hd,
+                        double A, double* dst, const double* src, cudaStream_t s);
 cudaError_t adj_lincomb(long long n, double* out, int nt, const double* const* x, const double* c,
                         double b, cudaStream_t s);
 cudaError_t adj_sums(long long n, const double* x, double* out, cudaStream_t s);
@@ -167,6 +170,12 @@ mf_status cuda_fail(mf_problem* pb, cudaError_t e, const char* what) {
   do {                                                      \
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return cuda_fail(pb, e_, #call); \
+  } while (0)
+
+#define MF_TRY_STATUS(x)             \
+  do {                               \
+    mf_status r_ = (x);              \
+    if (r_ != MF_OK) return r_;      \
   } while (0)
 
 mf_status read_state(mf_problem* pb, SolverState* s) {
@@ -932,7 +941,8 @@ mf_status mf_checkpoint_restore(mf_problem* pb, const void* src) {
 // one launch of the film's adjoint kernel: the outside iteration alone (g null) or the whole
 // right-hand side's vector-Jacobian product
 static mf_status film_adjoint(mf_problem* pb, int iters, const double* d_v, double* d_hin_bar,
-                              const double* d_g, double* d_gbar, double* d_jcbar, double* sbar) {
+                              const double* d_g, double* d_gbar, double* d_jcbar,
+                              const double* d_wbar_out, double* d_wbar_in, double* sbar) {
   if (pb->d.dim != 2 || pb->d.nout <= 0) {
     pb->err = "the film adjoint needs a film with free space";
     return MF_ERR_ARG;
@@ -940,7 +950,7 @@ static mf_status film_adjoint(mf_problem* pb, int iters, const double* d_v, doub
   MF_CUDA(pb, cudaSetDevice(pb->device));
   MF_CUDA(pb, cudaMemsetAsync(pb->d.gb, 0, sizeof(GridBarrier), pb->stream));
   cudaError_t e = film_adjoint_launch(pb->d.precision, pb->d, d_v, d_hin_bar, pb->scratch_m, iters,
-                                      d_g, d_gbar, d_jcbar, pb->stream);
+                                      d_g, d_gbar, d_jcbar, d_wbar_out, d_wbar_in, pb->stream);
   if (e != cudaSuccess) return cuda_fail(pb, e, "adjoint kernel launch");
   mf_status r = launch_finish(pb);
   if (r == MF_OK && sbar) {
@@ -954,39 +964,82 @@ mf_status mf_film_outside_vjp(mf_problem* pb, int iters, const double* d_v, doub
                               double* sbar) {
   Range range_("mf_film_outside_vjp");
   if (!pb || !d_v || !d_hin_bar || iters < 1) return MF_ERR_ARG;
-  return film_adjoint(pb, iters, d_v, d_hin_bar, nullptr, nullptr, nullptr, sbar);
+  return film_adjoint(pb, iters, d_v, d_hin_bar, nullptr, nullptr, nullptr, nullptr, nullptr, sbar);
 }
 
 mf_status mf_film_rhs_vjp(mf_problem* pb, int iters, const double* d_g, const double* d_v,
                           double* d_gbar, double* d_jcbar, double* sbar) {
   Range range_("mf_film_rhs_vjp");
   if (!pb || !d_g || !d_v || !d_gbar || !d_jcbar || iters < 1) return MF_ERR_ARG;
-  return film_adjoint(pb, iters, d_v, nullptr, d_g, d_gbar, d_jcbar, sbar);
+  return film_adjoint(pb, iters, d_v, nullptr, d_g, d_gbar, d_jcbar, nullptr, nullptr, sbar);
 }
 
-size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps) {
-  if (!pb || n_steps < 1 || pb->d.dim != 2) return 0;
-  return ((size_t)n_steps + 11) * (size_t)pb->d.ncell * sizeof(double) + 64;
+mf_status mf_film_rhs_vjp_warm(mf_problem* pb, int iters, const double* d_g, const double* d_v,
+                               const double* d_wbar_out, double* d_gbar, double* d_jcbar,
+                               double* d_wbar_in, double* sbar) {
+  Range range_("mf_film_rhs_vjp_warm");
+  if (!pb || !d_g || !d_v || !d_gbar || !d_jcbar || iters < 1) return MF_ERR_ARG;
+  return film_adjoint(pb, iters, d_v, nullptr, d_g, d_gbar, d_jcbar, d_wbar_out, d_wbar_in, sbar);
 }
 
-mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const double* t_steps,
-                                 const double* h_steps, const double* d_g0, const double* d_target,
-                                 void* d_work, size_t work_bytes, double* d_jcbar,
-                                 double* knots_bar, double* loss) {
+// the warm start of the next film right-hand side (the most recent call's iterate, its shift
+// applied) as an FP64 free-space field, or a given field made the warm start
+static mf_status warm_save(mf_problem* pb, double* dst) {
+  SolverState s;
+  MF_TRY_STATUS(read_state(pb, &s));
+  void* hd = s.hd_sel ? pb->d.hd2 : pb->d.hd;
+  cudaError_t e = adj_warm_io(pb->d.precision, pb->d.ncell, 0, pb->d.mask, hd, s.A_prev, dst, nullptr,
+                              pb->stream);
+  return e == cudaSuccess ? MF_OK : cuda_fail(pb, e, "warm start save");
+}
+static mf_status warm_load(mf_problem* pb, const double* src) {
+  SolverState s;
+  MF_TRY_STATUS(read_state(pb, &s));
+  s.hd_sel = 0; s.warm_valid = 1; s.A_prev = 0.0; s.com_valid = 0; s.A_com = 0.0;
+  cudaError_t e = adj_warm_io(pb->d.precision, pb->d.ncell, 1, pb->d.mask, pb->d.hd, 0.0, nullptr, src,
+                              pb->stream);
+  if (e != cudaSuccess) return cuda_fail(pb, e, "warm start load");
+  return write_state(pb, &s);
+}
+
+size_t mf_film_solve_gradient_work_bytes(const mf_problem* pb, int n_steps, int ckpt_every) {
+  if (!pb || n_steps < 1 || ckpt_every < 1 || pb->d.dim != 2) return 0;
+  const size_t C = (size_t)std::min(ckpt_every, n_steps);
+  const size_t S = ((size_t)n_steps + C - 1) / C;
+  // 2 fields per checkpoint (state, warm start), 3 stage inputs per step of a segment, 12 more
+  return (2 * S + 3 * C + 12) * (size_t)pb->d.ncell * sizeof(double) + 64;
+}
+
+mf_status mf_film_solve_gradient(mf_problem* pb, int n_steps, const double* t_steps,
+                                 const double* h_steps, const int* iters, int ckpt_every,
+                                 const double* d_g0, const double* d_warm0, const double* d_target,
+                                 void* d_work, size_t work_bytes, double* d_jcbar, double* knots_bar,
+                                 int n_knots, double* d_warm0_bar, double* loss) {
   Range range_("mf_film_solve_gradient");
-  if (!pb || iters < 1 || n_steps < 1 || !t_steps || !h_steps || !d_g0 || !d_target || !d_work ||
-      !d_jcbar || !knots_bar || !loss)
+  if (!pb || n_steps < 1 || ckpt_every < 1 || !t_steps || !h_steps || !iters || !d_g0 ||
+      !d_target || !d_work || !loss)
     return MF_ERR_ARG;
   if (pb->d.dim != 2 || pb->d.nout <= 0 || pb->p.he_knots < 2) {
     pb->err = "the solve gradient needs a film with free space and a piecewise-linear h_e";
     return MF_ERR_ARG;
   }
-  if (work_bytes < mf_film_solve_gradient_work_bytes(pb, n_steps)) {
+  const bool want_grad = d_jcbar != nullptr || knots_bar != nullptr || d_warm0_bar != nullptr;
+  if (want_grad && (!d_jcbar || !knots_bar || (d_warm0_bar && !d_warm0))) {
+    pb->err = "a gradient needs d_jcbar and knots_bar (and d_warm0 for d_warm0_bar)";
+    return MF_ERR_ARG;
+  }
+  const int K = pb->p.he_knots;
+  if (knots_bar && n_knots != K) {
+    pb->err = "n_knots differs from the problem's number of h_e knots";
+    return MF_ERR_ARG;
+  }
+  for (int i = 0; i < 3 * n_steps; ++i)
+    if (iters[i] < 1) { pb->err = "every call needs at least one outside iteration"; return MF_ERR_ARG; }
+  if (work_bytes < mf_film_solve_gradient_work_bytes(pb, n_steps, ckpt_every)) {
     pb->err = "work buffer smaller than mf_film_solve_gradient_work_bytes";
     return MF_ERR_WORKSPACE;
   }
   MF_CUDA(pb, cudaSetDevice(pb->device));
-  const int K = pb->p.he_knots;
   std::vector<double> kn(2 * K);
   MF_CUDA(pb, cudaMemcpyAsync(kn.data(), pb->d.he_t, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, pb->stream));
   MF_CUDA(pb, cudaStreamSynchronize(pb->stream));
@@ -1005,18 +1058,23 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const d
   }
   const long long n = pb->d.ncell;
   const cudaStream_t st = pb->stream;
-  double* Y = (double*)d_work;                 // states Y_0 .. Y_N
-  double* K1 = Y + (size_t)(n_steps + 1) * n;
+  const int C = std::min(ckpt_every, n_steps);
+  const int S = (n_steps + C - 1) / C;
+  double* CKY = (double*)d_work;                // S checkpointed states
+  double* CKW = CKY + (size_t)S * n;            // S checkpointed warm starts
+  double* GS = CKW + (size_t)S * n;             // 3 C stage inputs of one segment
+  double* Y = GS + (size_t)3 * C * n;
+  double* K1 = Y + n;
   double* K2 = K1 + n;
   double* K3 = K2 + n;
-  double* Y2 = K3 + n;
-  double* Y3 = Y2 + n;
-  double* LAM = Y3 + n;
+  double* LAM = K3 + n;
   double* V = LAM + n;
-  double* G2 = V + n;
-  double* G3 = G2 + n;
-  double* TMP = G3 + n;
-  double* SC = TMP + n;                         // 2 device scalars
+  double* G = V + n;
+  double* JT = G + n;
+  double* TMP = JT + n;
+  double* OM0 = TMP + n;                        // cotangents of the warm start, in turn
+  double* OM1 = OM0 + n;
+  double* SC = OM1 + n;                         // 2 device scalars
   const double b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
   auto lin = [&](double* out, std::initializer_list<std::pair<const double*, double>> terms,
                  double c = 0.0) -> mf_status {
@@ -1027,77 +1085,118 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int iters, int n_steps, const d
     cudaError_t e = adj_lincomb(n, out, m, x, co, c, st);
     return e == cudaSuccess ? MF_OK : cuda_fail(pb, e, "lincomb");
   };
-  // f with a cold start and the fixed count (a forced count may end above the stop test)
-  auto f = [&](const double* y, double* out, int i) -> mf_status {
-    mf_status r = mf_reset_warm(pb);
-    if (r != MF_OK) return r;
-    r = mf_rhs_ex(pb, t_steps[i], seg[i], y, out, iters, nullptr);
-    return r == MF_ERR_NOCONV ? MF_OK : r;
+  // a call as the integrator makes it, with its frozen count; the stop tolerance is set to 0
+  // for the duration so that a count that ends above it neither fails nor drops the warm start
+  const double tol_saved = pb->d.iter_tol;
+  auto set_tol = [&](double tol) -> mf_status {
+    pb->d.iter_tol = tol;
+    MF_CUDA(pb, cudaMemcpyAsync((void*)pb->d.dev, &pb->d, sizeof(Desc), cudaMemcpyHostToDevice, st));
+    return MF_OK;
   };
-#define MF_TRY(x) do { mf_status r_ = (x); if (r_ != MF_OK) return r_; } while (0)
-  MF_CUDA(pb, cudaMemcpyAsync(Y, d_g0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  // forward over the frozen steps, keeping every state
-  for (int i = 0; i < n_steps; ++i) {
+  auto f = [&](const double* y, double* out, int step, int call) -> mf_status {
+    return mf_rhs_ex(pb, t_steps[step], seg[step], y, out, iters[call], nullptr);
+  };
+  auto start_warm = [&](int s) -> mf_status {        // the warm start of segment s's first call
+    if (s == 0 && !d_warm0) return mf_reset_warm(pb);
+    return warm_load(pb, s == 0 ? d_warm0 : CKW + (size_t)s * n);
+  };
+  // one step from Y (kept stage inputs in gs when non-null)
+  auto step_fwd = [&](int i, double* gs) -> mf_status {
     const double h = h_steps[i];
-    double* y = Y + (size_t)i * n;
-    MF_TRY(f(y, K1, i));
-    MF_TRY(lin(Y2, {{y, 1.0}, {K1, 0.5 * h}}));
-    MF_TRY(f(Y2, K2, i));
-    MF_TRY(lin(Y3, {{y, 1.0}, {K2, 0.75 * h}}));
-    MF_TRY(f(Y3, K3, i));
-    MF_TRY(lin(y + n, {{y, 1.0}, {K1, h * b1}, {K2, h * b2}, {K3, h * b3}}));
-  }
-  // loss and the cotangent of the final state: res = h_z(T) - target, lambda = dA K_h res
-  const double T = t_steps[n_steps - 1] + h_steps[n_steps - 1];
-  int kT = (int)(std::upper_bound(kt, kt + K, T) - kt) - 1;
-  kT = std::min(std::max(kT, 0), K - 2);
-  const double wT = (T - kt[kT]) / (kt[kT + 1] - kt[kT]);
-  const double heT = kv[kT] + wT * (kv[kT + 1] - kv[kT]);
-  const double dA = pb->d.dx * pb->d.dy;
-  MF_TRY(mf_readout_of(pb, MF_READ_HZ, T, Y + (size_t)n_steps * n, TMP));
-  MF_TRY(lin(TMP, {{TMP, 1.0}, {d_target, -1.0}}));
-  double sums[2];
-  {
-    cudaError_t e = adj_sums(n, TMP, SC, st);
-    if (e != cudaSuccess) return cuda_fail(pb, e, "sums");
-  }
-  MF_CUDA(pb, cudaMemcpyAsync(sums, SC, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (gs) MF_CUDA(pb, cudaMemcpyAsync(gs, Y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    MF_TRY_STATUS(f(Y, K1, i, 3 * i));
+    double* y2 = gs ? gs + n : TMP;
+    MF_TRY_STATUS(lin(y2, {{Y, 1.0}, {K1, 0.5 * h}}));
+    MF_TRY_STATUS(f(y2, K2, i, 3 * i + 1));
+    double* y3 = gs ? gs + 2 * n : TMP;
+    MF_TRY_STATUS(lin(y3, {{Y, 1.0}, {K2, 0.75 * h}}));
+    MF_TRY_STATUS(f(y3, K3, i, 3 * i + 2));
+    return lin(Y, {{Y, 1.0}, {K1, h * b1}, {K2, h * b2}, {K3, h * b3}});
+  };
+  mf_status r = set_tol(0.0);
+  auto body = [&]() -> mf_status {
+    // forward over the frozen steps, a checkpoint (state and warm start) every C steps
+    MF_CUDA(pb, cudaMemcpyAsync(Y, d_g0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    MF_TRY_STATUS(start_warm(0));
+    for (int i = 0; i < n_steps; ++i) {
+      if (i % C == 0) {
+        MF_CUDA(pb, cudaMemcpyAsync(CKY + (size_t)(i / C) * n, Y, n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+        if (i > 0) MF_TRY_STATUS(warm_save(pb, CKW + (size_t)(i / C) * n));
+      }
+      MF_TRY_STATUS(step_fwd(i, nullptr));
+    }
+    // loss: res = h_z(T) - target
+    const double T = t_steps[n_steps - 1] + h_steps[n_steps - 1];
+    int kT = (int)(std::upper_bound(kt, kt + K, T) - kt) - 1;
+    kT = std::min(std::max(kT, 0), K - 2);
+    const double wT = (T - kt[kT]) / (kt[kT + 1] - kt[kT]);
+    const double heT = kv[kT] + wT * (kv[kT + 1] - kv[kT]);
+    const double dA = pb->d.dx * pb->d.dy;
+    MF_TRY_STATUS(mf_readout_of(pb, MF_READ_HZ, T, Y, TMP));
+    MF_TRY_STATUS(lin(TMP, {{TMP, 1.0}, {d_target, -1.0}}));
+    double sums[2];
+    {
+      cudaError_t e = adj_sums(n, TMP, SC, st);
+      if (e != cudaSuccess) return cuda_fail(pb, e, "sums");
+    }
+    MF_CUDA(pb, cudaMemcpyAsync(sums, SC, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(pb, cudaStreamSynchronize(st));
+    *loss = 0.5 * dA * sums[1];
+    if (!want_grad) return MF_OK;
+    for (int k = 0; k < K; ++k) knots_bar[k] = 0.0;
+    knots_bar[kT] += (1.0 - wT) * dA * sums[0];
+    knots_bar[kT + 1] += wT * dA * sums[0];
+    // cotangent of the final state: lambda = dA K_h res (h_z readout of res, minus its h_e)
+    MF_TRY_STATUS(mf_readout_of(pb, MF_READ_HZ, T, TMP, V));
+    MF_TRY_STATUS(lin(LAM, {{V, dA}}, -dA * heT));
+    MF_CUDA(pb, cudaMemsetAsync(d_jcbar, 0, n * sizeof(double), st));
+    const double* om = nullptr;                  // cotangent of the last call's iterate
+    double* om_next = OM0;
+    // reverse sweep, segment by segment: recompute the segment's stage inputs from its
+    // checkpoint, then the three products per step with the warm-start cotangent carried
+    for (int s = S - 1; s >= 0; --s) {
+      const int i0 = s * C, i1 = std::min(n_steps, i0 + C);
+      MF_CUDA(pb, cudaMemcpyAsync(Y, CKY + (size_t)s * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      MF_TRY_STATUS(start_warm(s));
+      for (int i = i0; i < i1; ++i) MF_TRY_STATUS(step_fwd(i, GS + (size_t)3 * (i - i0) * n));
+      for (int i = i1 - 1; i >= i0; --i) {
+        const double h = h_steps[i];
+        const double* g1 = GS + (size_t)3 * (i - i0) * n;
+        double sb[3];
+        auto vjp = [&](const double* g, int call, double* gbar, double* sbo) -> mf_status {
+          MF_TRY_STATUS(mf_film_rhs_vjp_warm(pb, iters[call], g, V, om, gbar, JT, om_next, sbo));
+          om = om_next;
+          om_next = om_next == OM0 ? OM1 : OM0;
+          return lin(d_jcbar, {{d_jcbar, 1.0}, {JT, 1.0}});
+        };
+        MF_TRY_STATUS(lin(V, {{LAM, h * b3}}));
+        MF_TRY_STATUS(vjp(g1 + 2 * n, 3 * i + 2, K3, &sb[2]));               // k3 = f(y + 3h/4 k2)
+        MF_TRY_STATUS(lin(V, {{LAM, h * b2}, {K3, 0.75 * h}}));
+        MF_TRY_STATUS(vjp(g1 + n, 3 * i + 1, K2, &sb[1]));                    // k2 = f(y + h/2 k1)
+        MF_TRY_STATUS(lin(V, {{LAM, h * b1}, {K2, 0.5 * h}}));
+        MF_TRY_STATUS(vjp(g1, 3 * i, K1, &sb[0]));                            // k1 = f(y)
+        MF_TRY_STATUS(lin(LAM, {{LAM, 1.0}, {K3, 1.0}, {K2, 1.0}, {K1, 1.0}}));
+        const int k = seg[i];
+        const double dt = kt[k + 1] - kt[k];
+        const double sbar = sb[0] + sb[1] + sb[2];                           // h_e_dot = slope of k
+        knots_bar[k + 1] += sbar / dt;
+        knots_bar[k] -= sbar / dt;
+      }
+    }
+    // a cold first call starts from h_e_dot on free space, whose cotangent sums to zero; a given
+    // first warm start gets its cotangent
+    if (d_warm0_bar)
+      MF_CUDA(pb, cudaMemcpyAsync(d_warm0_bar, om, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return MF_OK;
+  };
+  if (r == MF_OK) r = body();
+  const std::string err = pb->err;
+  const mf_status r2 = set_tol(tol_saved);
+  mf_reset_warm(pb);                            // the calls used the warm start's buffers
   MF_CUDA(pb, cudaStreamSynchronize(st));
-  *loss = 0.5 * dA * sums[1];
-  for (int k = 0; k < K; ++k) knots_bar[k] = 0.0;
-  knots_bar[kT] += (1.0 - wT) * dA * sums[0];
-  knots_bar[kT + 1] += wT * dA * sums[0];
-  MF_TRY(mf_readout_of(pb, MF_READ_HZ, T, TMP, V));                  // h_e(T) + K_h res
-  MF_TRY(lin(LAM, {{V, dA}}, -dA * heT));
-  MF_CUDA(pb, cudaMemsetAsync(d_jcbar, 0, n * sizeof(double), st));
-  // reverse sweep: recompute the stages from the kept state, then the three products
-  for (int i = n_steps - 1; i >= 0; --i) {
-    const double h = h_steps[i];
-    const double* y = Y + (size_t)i * n;
-    MF_TRY(f(y, K1, i));
-    MF_TRY(lin(Y2, {{y, 1.0}, {K1, 0.5 * h}}));
-    MF_TRY(f(Y2, K2, i));
-    MF_TRY(lin(Y3, {{y, 1.0}, {K2, 0.75 * h}}));
-    double sb[3];
-    MF_TRY(lin(V, {{LAM, h * b3}}));
-    MF_TRY(mf_film_rhs_vjp(pb, iters, Y3, V, G3, TMP, &sb[2]));        // k3 = f(Y3)
-    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
-    MF_TRY(lin(V, {{LAM, h * b2}, {G3, 0.75 * h}}));
-    MF_TRY(mf_film_rhs_vjp(pb, iters, Y2, V, G2, TMP, &sb[1]));        // k2 = f(Y2)
-    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
-    MF_TRY(lin(V, {{LAM, h * b1}, {G2, 0.5 * h}}));
-    MF_TRY(mf_film_rhs_vjp(pb, iters, y, V, K3, TMP, &sb[0]));         // k1 = f(Y_i)
-    MF_TRY(lin(d_jcbar, {{d_jcbar, 1.0}, {TMP, 1.0}}));
-    MF_TRY(lin(LAM, {{LAM, 1.0}, {G3, 1.0}, {G2, 1.0}, {K3, 1.0}}));
-    const int k = seg[i];
-    const double dt = kt[k + 1] - kt[k];
-    const double sbar = sb[0] + sb[1] + sb[2];                         // h_e_dot = slope of k
-    knots_bar[k + 1] += sbar / dt;
-    knots_bar[k] -= sbar / dt;
-  }
-#undef MF_TRY
-  MF_CUDA(pb, cudaStreamSynchronize(st));
-  return MF_OK;
+  pb->err = err;
+  return r != MF_OK ? r : r2;
 }
 
 mf_status mf_set_jc_map(mf_problem* pb, const double* d_jc) {
@@ -1119,10 +1218,14 @@ mf_status mf_set_jc_map(mf_problem* pb, const double* d_jc) {
   return MF_OK;
 }
 
-mf_status mf_set_knot_values(mf_problem* pb, const double* h_values) {
+mf_status mf_set_knot_values(mf_problem* pb, const double* h_values, int n_values) {
   if (!pb || !h_values) return MF_ERR_ARG;
   if (pb->p.he_knots < 1) {
     pb->err = "the problem's h_e is not piecewise linear";
+    return MF_ERR_ARG;
+  }
+  if (n_values != pb->p.he_knots) {
+    pb->err = "n_values differs from the problem's number of h_e knots";
     return MF_ERR_ARG;
   }
   MF_CUDA(pb, cudaSetDevice(pb->device));

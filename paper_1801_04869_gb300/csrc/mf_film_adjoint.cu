@@ -18,6 +18,13 @@
 //   end hbar_in = conductor * (hbar_0 - tot_0 / n_out),  sbar += (N / n_out) tot_0
 // The h_dot buffers of the warm start hold hbar and zbar, so the warm start is cleared.
 //
+// Warm-started calls (the integrator's: each call starts from the previous call's last iterate
+// instead of h_e_dot) add one input and one output to the linear map: the warm start on free
+// space and the last iterate h_{I-1}.  The cotangent of the last iterate (wbar_out, free space)
+// enters hbar_{I-1}; the cotangent of the warm start is out * (hbar_0 - tot_0 / n_out), written
+// beside hbar_in (wbar_in).  (Its sum over free space is zero, so a cold start, whose warm start
+// is h_e_dot on free space, adds nothing to sbar.)
+//
 // The full vector-Jacobian product of f(g; jc, h_e_dot) adds the nonlinear ends around it:
 //   j = (d_y g, -d_x g) is recomputed from g (Eq. 2; gradient column pass at the start, stored
 //   as two real fields), r = -conductor * hbar_in, ebar = (d_y r, -d_x r) (the transposed
@@ -37,6 +44,8 @@ struct AdjArgs {
   const double* g;      // full product: the state g (FP64, ncell); null: the outside iteration only
   double* gbar;         // full product: cotangent of g (FP64, ncell)
   double* jcbar;        // full product: cotangent of the jc map (FP64, ncell; 0 outside the film)
+  const double* wbar_out;  // cotangent of the last iterate (FP64, ncell, free space) or null
+  double* wbar_in;      // cotangent of the warm start (FP64, ncell, 0 on the conductor) or null
 };
 
 // full product, V1: gbar_{I-1} = conductor * v (with its sum) and g, forward of both
@@ -79,11 +88,17 @@ template <typename T>
 struct EpiRbar : EpiBase<T, T> {
   FilmPtrs<T> P;
   T t_q;
+  double* wdst;         // cotangent of the warm start (free space) or null
   __device__ void operator()(long long i, const V4<T>*, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     const V4<T> h = ld4(P.hd + i);
+    V4<double> w;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[0].v[q] = mask_at(m, q) != 0 ? -(h.v[q] - t_q) : (T)0;
+    for (int q = 0; q < 4; ++q) {
+      out[0].v[q] = mask_at(m, q) != 0 ? -(h.v[q] - t_q) : (T)0;
+      w.v[q] = mask_at(m, q) == 0 ? (double)(h.v[q] - t_q) : 0.0;
+    }
+    if (wdst) st4(wdst + i, w);
   }
 };
 
@@ -164,16 +179,22 @@ template <typename T>
 struct EpiPTh : EpiBase<T, T> {
   FilmPtrs<T> P;
   const T* zbar;        // null on the first backward iteration
+  const double* om;     // first backward iteration: cotangent of the last iterate, or null
   T s_q1;               // S / n_out
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     const V4<T> q1 = ldg4(P.q1 + i);
     V4<T> z;
     if (zbar) z = ld4(zbar + i);
+    else if (om) {
+      const V4<double> w = ld4(om + i);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) z.v[q] = mask_at(m, q) == 0 ? (T)w.v[q] : (T)0;
+    }
     V4<T> h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      h.v[q] = (zbar ? z.v[q] : (T)0) + in[0].v[q] - s_q1 * q1.v[q];
+      h.v[q] = ((zbar || om) ? z.v[q] : (T)0) + in[0].v[q] - s_q1 * q1.v[q];
       const bool o = mask_at(m, q) == 0;
       if (o) this->acc += h.v[q];
       out[0].v[q] = o ? -h.v[q] : (T)0;
@@ -209,14 +230,19 @@ template <typename T>
 struct EpiPTout : EpiBase<T, T> {
   FilmPtrs<T> P;
   double* dst;
+  double* wdst;         // cotangent of the warm start (free space) or null
   T t_q;
   __device__ void operator()(long long i, const V4<T>*, V4<T>*) {
     const uchar4 m = ldmask4(P.mask + i);
     const V4<T> h = ld4(P.hd + i);
-    V4<double> r;
+    V4<double> r, w;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) r.v[q] = mask_at(m, q) != 0 ? (double)(h.v[q] - t_q) : 0.0;
+    for (int q = 0; q < 4; ++q) {
+      r.v[q] = mask_at(m, q) != 0 ? (double)(h.v[q] - t_q) : 0.0;
+      w.v[q] = mask_at(m, q) == 0 ? (double)(h.v[q] - t_q) : 0.0;
+    }
     st4(dst + i, r);
+    if (wdst) st4(wdst + i, w);
   }
 };
 
@@ -266,6 +292,7 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
       const bool first = i == a.iters - 1;
       {
         EpiPTh<T> e; e.P = F.ptrs(); e.zbar = first ? nullptr : zbuf; e.s_q1 = (T)(S / nout);
+        e.om = first ? a.wbar_out : nullptr;
         if (i > 0) F.rows<1, 1>(F.rb1, F.Sa, F.Sb, e, 1);               // V3
         else F.rows<1, 0>(F.rb1, F.Sa, nullptr, e, 1);
       }
@@ -274,12 +301,12 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
       sbar += N / nout * tot;
       if (i == 0) {
         if (!full) {
-          EpiPTout<T> e; e.P = F.ptrs(); e.dst = a.hin_bar; e.t_q = (T)(tot / nout);
+          EpiPTout<T> e; e.P = F.ptrs(); e.dst = a.hin_bar; e.wdst = a.wbar_in; e.t_q = (T)(tot / nout);
           F.rows<0, 0>(F.rb1, nullptr, nullptr, e, -1);
           break;
         }
         {
-          EpiRbar<T> e; e.P = F.ptrs(); e.t_q = (T)(tot / nout);
+          EpiRbar<T> e; e.P = F.ptrs(); e.t_q = (T)(tot / nout); e.wdst = a.wbar_in;
           F.rows<0, 1>(F.rb1, nullptr, F.Sb, e, -1);                    // r
         }
         if (!F.sync(62)) { status = ST_BARRIER; break; }
@@ -383,11 +410,32 @@ cudaError_t adj_sums(long long n, const double* x, double* out, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// the warm start of a film right-hand side: dst = h_dot - A on free space, 0 elsewhere (FP64) for
+// save; h_dot = src on free space for load (the caller sets A = 0)
+template <typename T>
+__global__ void warm_io_kernel(long long n, int load, const uint8_t* mask, T* hd, double A,
+                               double* dst, const double* src) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool o = mask[i] == 0;
+    if (load) hd[i] = o ? (T)src[i] : (T)0;
+    else dst[i] = o ? (double)hd[i] - A : 0.0;
+  }
+}
+
+cudaError_t adj_warm_io(int precision, long long n, int load, const uint8_t* mask, void* hd,
+                        double A, double* dst, const double* src, cudaStream_t s) {
+  if (precision) warm_io_kernel<float><<<304, 256, 0, s>>>(n, load, mask, (float*)hd, A, dst, src);
+  else warm_io_kernel<double><<<304, 256, 0, s>>>(n, load, mask, (double*)hd, A, dst, src);
+  return cudaGetLastError();
+}
+
 cudaError_t film_adjoint_launch(int precision, const Desc& d, const double* v, double* hin_bar,
                                 double* sbar, int iters, const double* g, double* gbar,
-                                double* jcbar, cudaStream_t s) {
+                                double* jcbar, const double* wbar_out, double* wbar_in,
+                                cudaStream_t s) {
   const Desc* dg = d.dev;
-  AdjArgs a{v, hin_bar, sbar, iters, g, gbar, jcbar};
+  AdjArgs a{v, hin_bar, sbar, iters, g, gbar, jcbar, wbar_out, wbar_in};
   void* args[] = {&dg, &a};
   const size_t smem = film_smem_bytes(precision);
   const void* fn = precision ? (const void*)film_adjoint_kernel<float> : (const void*)film_adjoint_kernel<double>;

@@ -30,7 +30,7 @@ EXPORTS = ["mf_default_params", "mf_workspace_bytes", "mf_create", "mf_rhs", "mf
            "mf_autotune", "mf_batch_plan", "mf_checkpoint_bytes", "mf_checkpoint_save",
            "mf_checkpoint_restore", "mf_film_outside_vjp", "mf_film_rhs_vjp",
            "mf_film_solve_gradient_work_bytes", "mf_film_solve_gradient", "mf_set_jc_map",
-           "mf_set_knot_values", "mf_set_barrier_timeout"]
+           "mf_set_knot_values", "mf_set_barrier_timeout", "mf_film_rhs_vjp_warm"]
 
 
 class mf_params(ctypes.Structure):
@@ -110,11 +110,13 @@ def load() -> ctypes.CDLL:
         "mf_checkpoint_restore": (ctypes.c_int, [vp, vp]),
         "mf_film_outside_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, dp]),
         "mf_film_rhs_vjp": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, dp]),
-        "mf_film_solve_gradient_work_bytes": (ctypes.c_size_t, [vp, ctypes.c_int]),
+        "mf_film_rhs_vjp_warm": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, dp]),
+        "mf_film_solve_gradient_work_bytes": (ctypes.c_size_t, [vp, ctypes.c_int, ctypes.c_int]),
         "mf_set_jc_map": (ctypes.c_int, [vp, vp]),
-        "mf_set_knot_values": (ctypes.c_int, [vp, dp]),
-        "mf_film_solve_gradient": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp, vp, vp, vp,
-                                                  ctypes.c_size_t, vp, dp, dp]),
+        "mf_set_knot_values": (ctypes.c_int, [vp, dp, ctypes.c_int]),
+        "mf_film_solve_gradient": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, ip, ctypes.c_int, vp, vp,
+                                                  vp, vp, ctypes.c_size_t, vp, dp, ctypes.c_int, vp,
+                                                  dp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -313,21 +315,42 @@ class Problem:
                                              _dptr(jcbar), ctypes.byref(sb)))
         return gbar, jcbar, sb.value
 
-    def mf_film_solve_gradient(self, g0, target, steps, iters: int, n_knots: int):
-        """(loss, dL/djc as a device tensor, dL/dknot values as a list) of the frozen-step solve
-        over steps = [(t, h), ...]."""
+    def mf_film_rhs_vjp_warm(self, g, v, iters: int, wbar_out=None):
+        """Cotangents (of g, of the jc map, of the warm start as device tensors, of h_e_dot as a
+        float) of one warm-started film right-hand side with `iters` outside iterations."""
+        import torch
+        gbar, jcbar, wbar = torch.empty_like(v), torch.empty_like(v), torch.empty_like(v)
+        sb = ctypes.c_double(0.0)
+        self._check(self.lib.mf_film_rhs_vjp_warm(self.h, iters, _dptr(g), _dptr(v), _dptr(wbar_out),
+                                                  _dptr(gbar), _dptr(jcbar), _dptr(wbar),
+                                                  ctypes.byref(sb)))
+        return gbar, jcbar, wbar, sb.value
+
+    def mf_film_solve_gradient(self, g0, target, steps, iters, ckpt_every: int = 20, warm0=None,
+                               grad: bool = True, warm0_grad: bool = False):
+        """Loss of the frozen-step, frozen-count solve over steps = [(t, h), ...] with
+        iters = 3 outside-iteration counts per step; with grad, also dL/djc (device tensor),
+        dL/d(knot values) (list) and, with warm0_grad, dL/dwarm0 (device tensor).
+        Returns (loss, jcbar, knots_bar, warm0_bar) (None where not computed)."""
         import torch
         n = len(steps)
+        iters = [int(i) for i in iters]
+        if len(iters) != 3 * n:
+            raise ValueError(f"iters needs 3 counts per step ({3 * n}), got {len(iters)}")
+        K = self.params.he_knots
         ts = (ctypes.c_double * n)(*[float(t) for t, _ in steps])
         hs = (ctypes.c_double * n)(*[float(h) for _, h in steps])
-        nb = self.lib.mf_film_solve_gradient_work_bytes(self.h, n)
+        it = (ctypes.c_int * (3 * n))(*iters)
+        nb = self.lib.mf_film_solve_gradient_work_bytes(self.h, n, ckpt_every)
         work = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        jcbar = torch.empty_like(g0)
-        kb = (ctypes.c_double * max(n_knots, 1))()
+        jcbar = torch.empty_like(g0) if grad else None
+        kb = (ctypes.c_double * max(K, 1))() if grad else None
+        wb = torch.empty_like(g0) if (grad and warm0_grad) else None
         loss = ctypes.c_double(0.0)
-        self._check(self.lib.mf_film_solve_gradient(self.h, iters, n, ts, hs, _dptr(g0), _dptr(target),
-                                                    _dptr(work), nb, _dptr(jcbar), kb, ctypes.byref(loss)))
-        return loss.value, jcbar, list(kb)[:n_knots]
+        self._check(self.lib.mf_film_solve_gradient(
+            self.h, n, ts, hs, it, ckpt_every, _dptr(g0), _dptr(warm0), _dptr(target), _dptr(work),
+            nb, _dptr(jcbar), kb, K if grad else 0, _dptr(wb), ctypes.byref(loss)))
+        return loss.value, jcbar, (list(kb)[:K] if grad else None), wb
 
     def mf_set_jc_map(self, jc):
         """jc: device float64 tensor of the grid's cells."""
@@ -335,7 +358,9 @@ class Problem:
 
     def mf_set_knot_values(self, values):
         v = [float(x) for x in values]
-        self._check(self.lib.mf_set_knot_values(self.h, (ctypes.c_double * len(v))(*v)))
+        if len(v) != self.params.he_knots:
+            raise ValueError(f"the problem has {self.params.he_knots} knots, got {len(v)} values")
+        self._check(self.lib.mf_set_knot_values(self.h, (ctypes.c_double * len(v))(*v), len(v)))
 
     def mf_get_log(self, cap: int = 1 << 16):
         buf = (mf_step_log * cap)()

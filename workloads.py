@@ -213,6 +213,35 @@ def cube_bulk(n_grid: int = 128, precision: int = 1) -> Workload:
 
 
 
+def adjoint_film(n_grid: int = 1024, precision: int = 1, T: float = 0.1, knots: int = 16,
+                 jc_seed: int = 5) -> Workload:
+    """The film of the gradient (adjoint) workload: a square film of n_grid/2 cells per side,
+    Omega = [-1,1]^2, in an n_grid^2 periodic grid with D = [-2,2]^2, n = 30, a per-cell critical
+    current density exp(0.2 z - 0.02), z ~ N(0,1) i.i.d. (seed jc_seed), and h_e(t) piecewise
+    linear through `knots` knots evenly spaced on [0, T] with the baseline values 0.5 t / T."""
+    L = 2.0
+    m = film_mask(n_grid, n_grid, L, L, "rect", ax=1.0, ay=1.0)
+    kt = tuple(float(x) for x in np.linspace(0.0, T, knots))
+    kv = tuple(0.5 * t / T for t in kt)
+    wl = Workload(f"square_film_{n_grid // 2}_in_{n_grid}_adjoint", 2, n_grid, n_grid, 1, L, L, 0.0,
+                  m, n=30.0, rho_out=1.0, precision=precision, t0=0.0, t1=T, he_knots=(kt, kv))
+    wl.jc_map = jc_map_lognormal((n_grid, n_grid), seed=jc_seed, sigma=0.2)
+    return wl
+
+
+def segment_steps(knot_times, n_steps: int) -> list[tuple[float, float]]:
+    """n_steps (t, h) steps covering [t_0, t_last] of the knots, spread as evenly as whole numbers
+    allow over the segments and uniform inside each, so that no step crosses a knot."""
+    kt = [float(t) for t in knot_times]
+    nseg = len(kt) - 1
+    per = [n_steps // nseg + (1 if k < n_steps % nseg else 0) for k in range(nseg)]
+    steps = []
+    for k in range(nseg):
+        h = (kt[k + 1] - kt[k]) / per[k]
+        steps += [(kt[k] + i * h, h) for i in range(per[k])]
+    return steps
+
+
 def film_batch(count: int = 256, seed: int = 3, max_side: int = 512, precision: int = 1) -> list[Workload]:
     """Independent films of a parameter/geometry sweep: the shape class is uniform over
     {square, rectangle with aspect U[1, 2], disk}, the film side s (cells) over 64 .. max_side,
