@@ -58,8 +58,8 @@ def stop_test_counts(wl, jc, steps):
         for aa, kprev in ((0.0, None), (0.5, 0), (0.75, 1)):
             gs = y if kprev is None else y + aa * h * ks[kprev]
             kj, it, st = p.rhs(t, gs, k)
-            if st != 0:
-                raise SystemExit(f"the stop test failed at t = {t}")
+            if st != 0:          # the cap was reached: the frozen map uses the cap as the count
+                print(f"the stop test reached the cap ({it}) at t = {t}", flush=True)
             ks.append(kj)
             counts.append(int(it))
         y = y + h * (2.0 / 9.0 * ks[0] + 1.0 / 3.0 * ks[1] + 4.0 / 9.0 * ks[2])
