@@ -265,7 +265,8 @@ mf_status mf_set_knot_values(mf_problem* pb, const double* h_values, int n_value
    d_jcbar is not NULL, dL/djc per cell to d_jcbar (device FP64, nx*ny; zero outside the
    superconductor), dL/dv_k for the n_knots knot values of h_e to knots_bar (host; n_knots must
    equal he_knots) and, when d_warm0_bar is not NULL, dL/d(first warm start) (device FP64).
-   d_jcbar = knots_bar = d_warm0_bar = NULL computes the loss alone (forward only).  Memory: the
+   d_jcbar = knots_bar = d_warm0_bar = NULL computes the loss alone (forward only).  d_hz_T
+   (device FP64, nx*ny, may be NULL) receives h_z(T) of the forward.  Memory: the
    forward keeps a checkpoint (state and warm start) every ckpt_every steps in d_work (device, at
    least mf_film_solve_gradient_work_bytes(pb, n_steps, ckpt_every) bytes); the reverse sweep
    recomputes each segment's stage inputs from its checkpoint and runs mf_film_rhs_vjp_warm three
@@ -279,7 +280,7 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int n_steps, const double* t_st
                                  const double* h_steps, const int* iters, int ckpt_every,
                                  const double* d_g0, const double* d_warm0, const double* d_target,
                                  void* d_work, size_t work_bytes, double* d_jcbar, double* knots_bar,
-                                 int n_knots, double* d_warm0_bar, double* loss);
+                                 int n_knots, double* d_warm0_bar, double* d_hz_T, double* loss);
 
 /* Checkpoints: everything a continuation reads — the integrator state and counters, the six
    FP64 state/derivative buffers (with the first-same-as-last derivative), the outside

@@ -1014,7 +1014,7 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int n_steps, const double* t_st
                                  const double* h_steps, const int* iters, int ckpt_every,
                                  const double* d_g0, const double* d_warm0, const double* d_target,
                                  void* d_work, size_t work_bytes, double* d_jcbar, double* knots_bar,
-                                 int n_knots, double* d_warm0_bar, double* loss) {
+                                 int n_knots, double* d_warm0_bar, double* d_hz_T, double* loss) {
   Range range_("mf_film_solve_gradient");
   if (!pb || n_steps < 1 || ckpt_every < 1 || !t_steps || !h_steps || !iters || !d_g0 ||
       !d_target || !d_work || !loss)
@@ -1134,6 +1134,7 @@ mf_status mf_film_solve_gradient(mf_problem* pb, int n_steps, const double* t_st
     const double heT = kv[kT] + wT * (kv[kT + 1] - kv[kT]);
     const double dA = pb->d.dx * pb->d.dy;
     MF_TRY_STATUS(mf_readout_of(pb, MF_READ_HZ, T, Y, TMP));
+    if (d_hz_T) MF_CUDA(pb, cudaMemcpyAsync(d_hz_T, TMP, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     MF_TRY_STATUS(lin(TMP, {{TMP, 1.0}, {d_target, -1.0}}));
     double sums[2];
     {

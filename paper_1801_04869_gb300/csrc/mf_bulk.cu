@@ -381,7 +381,9 @@ struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 er
       if (err) {
         const double E = h * (-5.0 / 72.0 * k1[k] + 1.0 / 12.0 * k2[k] + 1.0 / 9.0 * k3[k] - 0.125 * g);
         const double sc = atol + rtol * fmax(fabs(y[k]), fabs(ynew[k]));
-        double q = fabs(E) / sc;
+        double q;                                            // the ratio in the transform precision
+        if constexpr (sizeof(T) == 4) q = (double)__fdiv_rn((float)fabs(E), (float)sc);
+        else q = fabs(E) / sc;
         if (!(q == q) || isinf(q)) q = 1e300;
         this->accmax = fmax(this->accmax, q);
       } else if (!isfinite(g)) {

@@ -12,6 +12,23 @@
 
 namespace mf {
 
+// The threads that run one transform together: the whole CTA (the default) or one half of it
+// (threads [NT/2 g, NT/2 g + NT/2)) with its own named barrier, so that the two halves work on
+// their own lines without waiting for each other.
+struct Cta {
+  __device__ __forceinline__ int tid() const { return threadIdx.x; }
+  static constexpr int nt = NT;
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct HalfCta {
+  int g;
+  __device__ __forceinline__ int tid() const { return threadIdx.x & (NT / 2 - 1); }
+  static constexpr int nt = NT / 2;
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "n"(NT / 2) : "memory");
+  }
+};
+
 template <typename T> struct Sqrt1_2;
 template <> struct Sqrt1_2<float> { static constexpr float v = 0.70710678118654752440f; };
 template <> struct Sqrt1_2<double> { static constexpr double v = 0.70710678118654752440; };
@@ -116,9 +133,9 @@ __device__ __forceinline__ void stage_twiddles(const C2<T>* __restrict__ twk, in
 // so a butterfly's R elements sit at one base plus multiples of a padded stride.  The same
 // holds with stride 1 when e is a multiple of R (R divides 16): the R outputs of a p = 1 stage
 // share one padding group.  Other strides (short lines) take sp() per element.
-template <typename T, int R, int LGR, int DIR>
+template <typename T, int R, int LGR, int DIR, class G = Cta>
 __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int lgL, int lgp, int nlines,
-                                          const C2<T>* __restrict__ tw) {
+                                          const C2<T>* __restrict__ tw, G grp = G()) {
   C2<T>* const S = dsm<T>();
   const int in = dsm_off(in_p), out = dsm_off(out_p);
   const int lgq = lgL - LGR;          // log2(L / R)
@@ -127,7 +144,7 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int l
   const int nb = nlines << lgq;       // butterflies in this stage
   const int qs = q + (q >> 4), ps = p + (p >> 4);
   const bool fast_in = lgq >= 4, fast_out = lgp == 0 || lgp >= 4;
-  for (int b = threadIdx.x; b < nb; b += NT) {
+  for (int b = grp.tid(); b < nb; b += G::nt) {
     const int line = b >> lgq, i = b & (q - 1);
     const int k = i & (p - 1);
     const int src = (line << lgL) + i;
@@ -157,16 +174,31 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int l
       for (int j = 0; j < R; ++j) S[out + sp(dst + (j << lgp))] = v[j];
     }
   }
-  __syncthreads();
+  grp.sync();
+}
+
+// radix 16 is used in single precision when a thread holds 16 values per stage
+template <typename T> constexpr bool kRadix16 = sizeof(T) == 4 && VPT >= 16;
+
+// one stage of radix 2^lgr (the plan's choice) through the matching instantiation
+template <typename T, int DIR, class G = Cta>
+__device__ __forceinline__ void fft_stage_any(int lgr, const C2<T>* in, C2<T>* out, int lgL, int lgp,
+                                              int nlines, const C2<T>* __restrict__ tw, G grp = G()) {
+  if constexpr (kRadix16<T>) {
+    if (lgr == 4) { fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw, grp); return; }
+  }
+  if (lgr == 3) fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw, grp);
+  else if (lgr == 2) fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw, grp);
+  else fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw, grp);
 }
 
 // Stages `first` .. m-1 of the FFT of nlines lines of length 2^lgL held in shared buffer `a`
 // (`b` is the second buffer of the autosort); returns the buffer that holds the result.  With
 // first = 1 the caller has done stage 0 itself (fft_first_io).  Must be called by all NT
 // threads of the CTA (it synchronises).
-template <typename T, int DIR>
+template <typename T, int DIR, class G = Cta>
 __device__ __noinline__ C2<T>* fft_lines_from(C2<T>* a, C2<T>* b, int lgL, int nlines,
-                                              const C2<T>* __restrict__ tw, int first) {
+                                              const C2<T>* __restrict__ tw, int first, G grp = G()) {
   int lgp = 0;
   int rem = lgL;
   int off = 0;                       // block of the current stage in the stage-ordered table
@@ -174,14 +206,11 @@ __device__ __noinline__ C2<T>* fft_lines_from(C2<T>* a, C2<T>* b, int lgL, int n
   C2<T>* out = b;
   for (int stage = 0; rem > 0; ++stage) {
     int l;
-    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) l = 4;
+    if (kRadix16<T> && rem >= 4 && rem != 5) l = 4;
     else if (rem >= 3) l = 3;
     else l = rem;
     if (stage >= first) {
-      if (sizeof(T) == 4 && l == 4) fft_stage<T, 16, 4, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      else if (l == 3) fft_stage<T, 8, 3, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      else if (l == 2) fft_stage<T, 4, 2, DIR>(in, out, lgL, lgp, nlines, tw + off);
-      else fft_stage<T, 2, 1, DIR>(in, out, lgL, lgp, nlines, tw + off);
+      fft_stage_any<T, DIR>(l, in, out, lgL, lgp, nlines, tw + off, grp);
       C2<T>* t = in; in = out; out = t;
     }
     off += ((1 << l) - 1) << lgp;
@@ -193,10 +222,10 @@ __device__ __noinline__ C2<T>* fft_lines_from(C2<T>* a, C2<T>* b, int lgL, int n
 // FFT of nlines lines of length 2^lgL held in shared buffer `a`, using `b` as the second
 // buffer of the autosort; returns the buffer that holds the result (a or b).  Must be called
 // by all NT threads of the CTA (it synchronises).
-template <typename T, int DIR>
+template <typename T, int DIR, class G = Cta>
 __device__ __forceinline__ C2<T>* fft_lines(C2<T>* a, C2<T>* b, int lgL, int nlines,
-                                            const C2<T>* __restrict__ tw) {
-  return fft_lines_from<T, DIR>(a, b, lgL, nlines, tw, 0);
+                                            const C2<T>* __restrict__ tw, G grp = G()) {
+  return fft_lines_from<T, DIR>(a, b, lgL, nlines, tw, 0, grp);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -225,7 +254,7 @@ __device__ __forceinline__ FftPlan fft_plan(int lgL) {
   int rem = lgL;
   while (rem > 0) {
     int l;
-    if (sizeof(T) == 4 && VPT >= 16 && rem >= 4 && rem != 5) l = 4;
+    if (kRadix16<T> && rem >= 4 && rem != 5) l = 4;
     else if (rem >= 3) l = 3;
     else l = rem;
     P.packed |= (unsigned)l << (4 * P.m);
@@ -237,14 +266,14 @@ __device__ __forceinline__ FftPlan fft_plan(int lgL) {
 
 // First stage of a transform (p = 1, no twiddles) reading its input through ld(line, pos) (global
 // memory) and writing shared buffer `out`.
-template <typename T, int R, int LGR, int DIR, class Ld>
-__device__ __forceinline__ void fft_first_io(int lgL, int nlines, Ld ld, C2<T>* out_p) {
+template <typename T, int R, int LGR, int DIR, class Ld, class G = Cta>
+__device__ __forceinline__ void fft_first_io(int lgL, int nlines, Ld ld, C2<T>* out_p, G grp = G()) {
   C2<T>* const S = dsm<T>();
   const int out = dsm_off(out_p);
   const int lgq = lgL - LGR;
   const int q = 1 << lgq;
   const int nb = nlines << lgq;
-  for (int b = threadIdx.x; b < nb; b += NT) {
+  for (int b = grp.tid(); b < nb; b += G::nt) {
     const int line = b >> lgq, i = b & (q - 1);
     C2<T> v[R];
 #pragma unroll
@@ -254,13 +283,13 @@ __device__ __forceinline__ void fft_first_io(int lgL, int nlines, Ld ld, C2<T>* 
 #pragma unroll
     for (int j = 0; j < R; ++j) S[a0 + j] = v[j];
   }
-  __syncthreads();
+  grp.sync();
 }
 // Last stage of a transform reading shared buffer `in` and writing through st(line, pos, v)
 // (global memory).
-template <typename T, int R, int LGR, int DIR, class St>
+template <typename T, int R, int LGR, int DIR, class St, class G = Cta>
 __device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp, int nlines,
-                                            const C2<T>* __restrict__ tw, St st) {
+                                            const C2<T>* __restrict__ tw, St st, G grp = G()) {
   C2<T>* const S = dsm<T>();
   const int in = dsm_off(in_p);
   const int lgq = lgL - LGR;
@@ -268,7 +297,7 @@ __device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp,
   const int p = 1 << lgp;
   const int nb = nlines << lgq;
   const int qs = q + (q >> 4);
-  for (int b = threadIdx.x; b < nb; b += NT) {
+  for (int b = grp.tid(); b < nb; b += G::nt) {
     const int line = b >> lgq, i = b & (q - 1);
     const int k = i & (p - 1);
     const int src = (line << lgL) + i;
@@ -292,42 +321,42 @@ __device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp,
 #pragma unroll
     for (int j = 0; j < R; ++j) st(line, dpos + (j << lgp), v[j]);
   }
-  __syncthreads();
+  grp.sync();
 }
 
-template <typename T, int DIR, class Ld>
-__device__ __forceinline__ void fft_first_io_any(int lgr, int lgL, int nlines, Ld ld, C2<T>* out) {
-  if constexpr (sizeof(T) == 4) {
-    if (lgr == 4) { fft_first_io<T, 16, 4, DIR>(lgL, nlines, ld, out); return; }
+template <typename T, int DIR, class Ld, class G = Cta>
+__device__ __forceinline__ void fft_first_io_any(int lgr, int lgL, int nlines, Ld ld, C2<T>* out, G grp = G()) {
+  if constexpr (kRadix16<T>) {
+    if (lgr == 4) { fft_first_io<T, 16, 4, DIR>(lgL, nlines, ld, out, grp); return; }
   }
-  if (lgr == 3) fft_first_io<T, 8, 3, DIR>(lgL, nlines, ld, out);
-  else if (lgr == 2) fft_first_io<T, 4, 2, DIR>(lgL, nlines, ld, out);
-  else fft_first_io<T, 2, 1, DIR>(lgL, nlines, ld, out);
+  if (lgr == 3) fft_first_io<T, 8, 3, DIR>(lgL, nlines, ld, out, grp);
+  else if (lgr == 2) fft_first_io<T, 4, 2, DIR>(lgL, nlines, ld, out, grp);
+  else fft_first_io<T, 2, 1, DIR>(lgL, nlines, ld, out, grp);
 }
-template <typename T, int DIR, class St>
+template <typename T, int DIR, class St, class G = Cta>
 __device__ __forceinline__ void fft_last_io_any(int lgr, const C2<T>* in, int lgL, int lgp, int nlines,
-                                                const C2<T>* __restrict__ tw, St st) {
-  if constexpr (sizeof(T) == 4) {
-    if (lgr == 4) { fft_last_io<T, 16, 4, DIR>(in, lgL, lgp, nlines, tw, st); return; }
+                                                const C2<T>* __restrict__ tw, St st, G grp = G()) {
+  if constexpr (kRadix16<T>) {
+    if (lgr == 4) { fft_last_io<T, 16, 4, DIR>(in, lgL, lgp, nlines, tw, st, grp); return; }
   }
-  if (lgr == 3) fft_last_io<T, 8, 3, DIR>(in, lgL, lgp, nlines, tw, st);
-  else if (lgr == 2) fft_last_io<T, 4, 2, DIR>(in, lgL, lgp, nlines, tw, st);
-  else fft_last_io<T, 2, 1, DIR>(in, lgL, lgp, nlines, tw, st);
+  if (lgr == 3) fft_last_io<T, 8, 3, DIR>(in, lgL, lgp, nlines, tw, st, grp);
+  else if (lgr == 2) fft_last_io<T, 4, 2, DIR>(in, lgL, lgp, nlines, tw, st, grp);
+  else fft_last_io<T, 2, 1, DIR>(in, lgL, lgp, nlines, tw, st, grp);
 }
 
 // the fused middle pass: forward last stage (radix R) on NFI input fields, mul(l, pos, x[], y[])
 // per position, inverse first stage on NFO output fields.  Shared line f * nl + l holds field
 // f of line group l.
-template <typename T, int R, int LGR, int NFI, int NFO, class Mul>
+template <typename T, int R, int LGR, int NFI, int NFO, class Mul, class G = Cta>
 __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int lgL, int nl,
-                                           const C2<T>* __restrict__ tw, Mul mul) {
+                                           const C2<T>* __restrict__ tw, Mul mul, G grp = G()) {
   C2<T>* const S = dsm<T>();
   const int in = dsm_off(in_p), out = dsm_off(out_p);
   const int lgq = lgL - LGR;
   const int q = 1 << lgq;
   const int nb = nl << lgq;
   const int qs = q + (q >> 4);
-  for (int b = threadIdx.x; b < nb; b += NT) {
+  for (int b = grp.tid(); b < nb; b += G::nt) {
     const int l = b >> lgq, i = b & (q - 1);
     C2<T> x[NFI][R];
     // twiddles of the last forward stage (p = q, k = i), from its block of the table
@@ -366,27 +395,27 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int 
       for (int j = 0; j < R; ++j) S[a0 + j] = y[g][j];
     }
   }
-  __syncthreads();
+  grp.sync();
 }
 
-template <typename T, int NFI, int NFO, class Mul>
+template <typename T, int NFI, int NFO, class Mul, class G = Cta>
 __device__ __forceinline__ void fft_middle_any(int lgr, const C2<T>* in, C2<T>* out, int lgL, int nl,
-                                               const C2<T>* __restrict__ tw, Mul mul) {
-  if constexpr (sizeof(T) == 4) {
-    if (lgr == 4) { fft_middle<T, 16, 4, NFI, NFO>(in, out, lgL, nl, tw, mul); return; }
+                                               const C2<T>* __restrict__ tw, Mul mul, G grp = G()) {
+  if constexpr (kRadix16<T>) {
+    if (lgr == 4) { fft_middle<T, 16, 4, NFI, NFO>(in, out, lgL, nl, tw, mul, grp); return; }
   }
-  if (lgr == 3) fft_middle<T, 8, 3, NFI, NFO>(in, out, lgL, nl, tw, mul);
-  else if (lgr == 2) fft_middle<T, 4, 2, NFI, NFO>(in, out, lgL, nl, tw, mul);
-  else fft_middle<T, 2, 1, NFI, NFO>(in, out, lgL, nl, tw, mul);
+  if (lgr == 3) fft_middle<T, 8, 3, NFI, NFO>(in, out, lgL, nl, tw, mul, grp);
+  else if (lgr == 2) fft_middle<T, 4, 2, NFI, NFO>(in, out, lgL, nl, tw, mul, grp);
+  else fft_middle<T, 2, 1, NFI, NFO>(in, out, lgL, nl, tw, mul, grp);
 }
 
 // Round trip F^-1[M F(.)] of NFI -> NFO fields on nl line groups:
 // gsrc(f, l) / gdst(g, l) give the first element of field f / g of group l (contiguous lines,
 // global or shared memory); after_first() runs (in every thread) once the first stage has
 // consumed the source.  Needs a plan of at least two stages.
-template <typename T, int NFI, int NFO, class Src, class Dst, class Mul, class AfterFirst>
+template <typename T, int NFI, int NFO, class Src, class Dst, class Mul, class AfterFirst, class G = Cta>
 __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T>* __restrict__ tw,
-                               Src gsrc, Dst gdst, Mul mul, AfterFirst after_first) {
+                               Src gsrc, Dst gdst, Mul mul, AfterFirst after_first, G grp = G()) {
   const FftPlan P = fft_plan<T>(lgL);
   const int m = P.m;
   // blocks of the stage-ordered tables: table A (plan order) starts at 0, table B (reversed
@@ -401,7 +430,7 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
   // forward stage 0: source -> sa
   const int l0 = P.lgr(0);
   fft_first_io_any<T, -1>(l0, lgL, NFI * nl,
-      [=](int line, int pos) { const int f = line / nl; return lds_c2(gsrc(f, line - f * nl) + pos); }, sa);
+      [=](int line, int pos) { const int f = line / nl; return lds_c2(gsrc(f, line - f * nl) + pos); }, sa, grp);
   after_first();                     // the source of the first stage is no longer needed
   offA += ((1 << l0) - 1) << lgp;
   lgp += l0;
@@ -409,35 +438,27 @@ __device__ void fft_round_trip(C2<T>* sa, C2<T>* sb, int lgL, int nl, const C2<T
   C2<T>* oth = sb;
   for (int s = 1; s < m - 1; ++s) {
     const int lgr = P.lgr(s);
-    const C2<T>* t = tw + offA;
-    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, -1>(cur, oth, lgL, lgp, NFI * nl, t);
-    else if (lgr == 3) fft_stage<T, 8, 3, -1>(cur, oth, lgL, lgp, NFI * nl, t);
-    else if (lgr == 2) fft_stage<T, 4, 2, -1>(cur, oth, lgL, lgp, NFI * nl, t);
-    else fft_stage<T, 2, 1, -1>(cur, oth, lgL, lgp, NFI * nl, t);
+    fft_stage_any<T, -1>(lgr, cur, oth, lgL, lgp, NFI * nl, tw + offA, grp);
     offA += ((1 << lgr) - 1) << lgp;
     lgp += lgr;
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // forward last stage + multiplier + inverse first stage (p = 1: no twiddles)
   const int lm = P.lgr(m - 1);
-  fft_middle_any<T, NFI, NFO>(lm, cur, oth, lgL, nl, tw + offA, mul);
+  fft_middle_any<T, NFI, NFO>(lm, cur, oth, lgL, nl, tw + offA, mul, grp);
   { C2<T>* tt = cur; cur = oth; oth = tt; }
   int offB = lenA + ((1 << lm) - 1);  // table B block of the inverse stage after the fused one
   int lgpi = lm;
   for (int s = m - 2; s >= 1; --s) {
     const int lgr = P.lgr(s);
-    const C2<T>* t = tw + offB;
-    if (sizeof(T) == 4 && lgr == 4) fft_stage<T, 16, 4, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
-    else if (lgr == 3) fft_stage<T, 8, 3, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
-    else if (lgr == 2) fft_stage<T, 4, 2, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
-    else fft_stage<T, 2, 1, +1>(cur, oth, lgL, lgpi, NFO * nl, t);
+    fft_stage_any<T, +1>(lgr, cur, oth, lgL, lgpi, NFO * nl, tw + offB, grp);
     offB += ((1 << lgr) - 1) << lgpi;
     lgpi += lgr;
     C2<T>* tt = cur; cur = oth; oth = tt;
   }
   // inverse last stage: shared -> destination
   fft_last_io_any<T, +1>(l0, cur, lgL, lgpi, NFO * nl, tw + offB,
-      [=](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; });
+      [=](int line, int pos, C2<T> v) { const int g = line / nl; gdst(g, line - g * nl)[pos] = v; }, grp);
 }
 
 }  // namespace mf

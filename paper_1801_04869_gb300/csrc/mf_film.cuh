@@ -203,6 +203,50 @@ struct Film {
     __syncthreads();
   }
 
+  // ---- y pass of one line kx with a one-field multiplier, by half of the CTA (group g, its
+  // own line region of both shared buffers and its own named barrier) ----
+  __device__ __noinline__ void col_line_half(int kx, const C2<T>* Sin, C2<T>* Sout, int op, int g) {
+    const int ny = this->ny, half = this->half;
+    const T* const ktab = this->ktab;
+    const T* const gtab = this->gtab;
+    const T lam = (T)d.lam;
+    const C2<T>* const src0 = Sin + (long long)kx * ny;
+    C2<T>* const dst0 = Sout + (long long)kx * ny;
+    auto src = [=](int, int) { return src0; };
+    auto dst = [=](int, int) { return dst0; };
+    const T s = (T)1 / (T)ncell;
+    const T ky_scale = (T)(PI_D / d.Ly), g_half = (T)(0.5 * d.sigma * d.sigma);
+    const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
+    const int nkx = this->nkx;
+    (void)half;
+    fft_round_trip<T, 1, 1>(sm + sp(g << lgy), sm2 + sp(g << lgy), lgy, 1, twy, src, dst,
+        [=](int, int ky, const C2<T>* x, C2<T>* y) {
+          T kyv, gy;
+          if constexpr (sizeof(T) == 4) {
+            kyv = (T)(ky < ny / 2 ? ky : ky - ny) * ky_scale;
+            gy = __expf(-kyv * kyv * g_half);
+          } else {
+            kyv = ldg_tab(&ktab[nkx + ky]);
+            gy = ldg_tab(&gtab[nkx + ky]);
+          }
+          const T k2 = kxv * kxv + kyv * kyv;
+          T kabs, kinv;
+          if constexpr (sizeof(T) == 4) {
+            kinv = k2 > (T)0 ? rsqrtf(k2) : (T)0;
+            kabs = k2 * kinv;
+          } else {
+            kabs = sqrt(k2);
+            kinv = k2 > (T)0 ? (T)1 / kabs : (T)0;
+          }
+          T m;
+          if (op == OP_K1) m = (T)2 * kinv;
+          else if (op == OP_K2) m = lam * kabs * (T)0.5 * (gx * gy);
+          else if (op == OP_KH) m = kabs * (T)0.5;
+          else m = (T)1;
+          y[0] = cscale(x[0], m * s);
+        }, [] {}, HalfCta{g});
+  }
+
   // lines per column item: fill the shared batch (two lines for single-field operators)
   __device__ int col_lines(int nf) const {
     int nl = BATCH / (nf * ny);
@@ -212,6 +256,15 @@ struct Film {
   __device__ void cols(const C2<T>* Sin, int nin, C2<T>* Sout, int nout, int op) {
     const int nl = col_lines(nin > nout ? nin : nout);
     const int nitems = (nkx + nl - 1) / nl;
+    if (nin == 1 && nout == 1 && nl == 2 && fft_plan<T>(lgy).m >= 2) {
+      // one line per half of the CTA: the halves run their transforms independently
+      const int g = (int)threadIdx.x / (NT / 2);
+      for (int it = vb; it < nitems; it += (int)nblocks) {
+        const int kx = it * 2 + g;
+        if (kx < nkx) col_line_half(kx, Sin, Sout, op, g);
+      }
+      return;
+    }
     for (int it = vb; it < nitems; it += (int)nblocks) {
       const int kx0 = it * nl;
       col_item(kx0, kx0 + nl <= nkx ? nl : nkx - kx0, Sin, nin, Sout, nout, op);
@@ -490,7 +543,12 @@ struct EpiFinal : EpiBase<T> {
       for (int q = 0; q < 4; ++q) {
         const double E = h * (-5.0 / 72.0 * a1.v[q] + 1.0 / 12.0 * a2.v[q] + 1.0 / 9.0 * a3.v[q] - 0.125 * g.v[q]);
         const double sc = atol + rtol * fmax(fabs(yy.v[q]), fabs(yn.v[q]));
-        double r = fabs(E) / sc;
+        // E and its scale in FP64; their ratio, which only feeds the accept test and the step
+        // size factor, in the transform precision (FP64 division runs at a small fraction of the
+        // FP32 rate on this part)
+        double r;
+        if constexpr (sizeof(T) == 4) r = (double)__fdiv_rn((float)fabs(E), (float)sc);
+        else r = fabs(E) / sc;
         if (!(r == r) || isinf(r)) r = 1e300;                // non-finite -> rejected step
         this->accmax = fmax(this->accmax, r);
       }

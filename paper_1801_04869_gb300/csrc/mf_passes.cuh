@@ -37,11 +37,11 @@ __device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
 // straight from global memory, all of a butterfly's loads in flight together: position m of
 // a packed line is A[m] + i B[m] for m <= nx/2 and conj(A[nx-m]) + i conj(B[nx-m]) above,
 // with the imaginary parts of the real DC and Nyquist terms dropped.
-template <typename T, int NIN>
+template <typename T, int NIN, class G = Cta>
 __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, const C2<T>* src,
                                                       long long fstride, long long kstride,
                                                       int npair, int lgpair, int lgx,
-                                                      const C2<T>* __restrict__ twx) {
+                                                      const C2<T>* __restrict__ twx, G grp = G()) {
   const int nx = 1 << lgx, half = nx >> 1;
   auto ld = [=](int line, int m) -> C2<T> {
     const int f = line >> lgpair, pr = line & (npair - 1);
@@ -54,23 +54,23 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
   };
   const FftPlan P = fft_plan<T>(lgx);
   const int l0 = P.lgr(0);
-  fft_first_io_any<T, +1>(l0, lgx, NIN * npair, ld, sm);
-  return fft_lines_from<T, +1>(sm, sm2, lgx, NIN * npair, twx, 1);
+  fft_first_io_any<T, +1>(l0, lgx, NIN * npair, ld, sm, grp);
+  return fft_lines_from<T, +1>(sm, sm2, lgx, NIN * npair, twx, 1, grp);
 }
 
 // Forward-transform NOUT fields of packed row pairs (in `sm_in`, second buffer `sm2`) along x
 // and scatter their half spectra.
-template <typename T, int NOUT>
+template <typename T, int NOUT, class G = Cta>
 __device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C2<T>* dst,
                                                      long long fstride, long long kstride,
                                                      int npair, int lgpair, int lgx,
-                                                     const C2<T>* __restrict__ twx) {
+                                                     const C2<T>* __restrict__ twx, G grp = G()) {
   const int nx = 1 << lgx, half = nx >> 1;
-  const C2<T>* sm = fft_lines<T, -1>(sm_in, sm2, lgx, NOUT * npair, twx);
+  const C2<T>* sm = fft_lines<T, -1>(sm_in, sm2, lgx, NOUT * npair, twx, grp);
   C2<T>* const S = dsm<T>();
   const int io = dsm_off(sm);
   const int per_f = npair * (half + 1);
-  for (int e = threadIdx.x; e < NOUT * per_f; e += NT) {
+  for (int e = grp.tid(); e < NOUT * per_f; e += G::nt) {
     const int f = e >= per_f ? (e >= 2 * per_f ? 2 : 1) : 0;
     const int rest = e - f * per_f;
     const int k = rest >> lgpair, pr = rest & (npair - 1);
@@ -82,7 +82,7 @@ __device__ __forceinline__ void rows_forward_scatter(C2<T>* sm_in, C2<T>* sm2, C
     o.b = C2<T>{hh * (zk.y + zm.y), hh * (zm.x - zk.x)};   // -i (zk - conj(zm)) / 2
     *(CPair<T>*)(dst + f * fstride + (long long)k * kstride + 2 * pr) = o;
   }
-  __syncthreads();
+  grp.sync();
 }
 
 // Load `n` contiguous lines of length L (line j at src + j * stride) into shared memory,

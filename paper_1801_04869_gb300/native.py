@@ -116,7 +116,7 @@ def load() -> ctypes.CDLL:
         "mf_set_knot_values": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         "mf_film_solve_gradient": (ctypes.c_int, [vp, ctypes.c_int, dp, dp, ip, ctypes.c_int, vp, vp,
                                                   vp, vp, ctypes.c_size_t, vp, dp, ctypes.c_int, vp,
-                                                  dp]),
+                                                  vp, dp]),
         "mf_get_log": (ctypes.c_int, [vp, P(mf_step_log), ctypes.c_longlong, P(ctypes.c_longlong)]),
         "mf_last_error": (ctypes.c_char_p, [vp]),
         "mf_destroy": (None, [vp]),
@@ -327,10 +327,11 @@ class Problem:
         return gbar, jcbar, wbar, sb.value
 
     def mf_film_solve_gradient(self, g0, target, steps, iters, ckpt_every: int = 20, warm0=None,
-                               grad: bool = True, warm0_grad: bool = False):
+                               grad: bool = True, warm0_grad: bool = False, hz_out=None):
         """Loss of the frozen-step, frozen-count solve over steps = [(t, h), ...] with
         iters = 3 outside-iteration counts per step; with grad, also dL/djc (device tensor),
-        dL/d(knot values) (list) and, with warm0_grad, dL/dwarm0 (device tensor).
+        dL/d(knot values) (list) and, with warm0_grad, dL/dwarm0 (device tensor); hz_out (a device
+        tensor of the grid, optional) receives h_z(T) of the forward.
         Returns (loss, jcbar, knots_bar, warm0_bar) (None where not computed)."""
         import torch
         n = len(steps)
@@ -349,7 +350,7 @@ class Problem:
         loss = ctypes.c_double(0.0)
         self._check(self.lib.mf_film_solve_gradient(
             self.h, n, ts, hs, it, ckpt_every, _dptr(g0), _dptr(warm0), _dptr(target), _dptr(work),
-            nb, _dptr(jcbar), kb, K if grad else 0, _dptr(wb), ctypes.byref(loss)))
+            nb, _dptr(jcbar), kb, K if grad else 0, _dptr(wb), _dptr(hz_out), ctypes.byref(loss)))
         return loss.value, jcbar, (list(kb)[:K] if grad else None), wb
 
     def mf_set_jc_map(self, jc):

@@ -89,7 +89,7 @@ def test_null_and_invalid_arguments_are_refused_without_a_gpu(lib):
     assert lib.mf_film_rhs_vjp_warm(None, 1, None, None, None, None, None, None, None) == native.MF_ERR_ARG
     assert lib.mf_set_barrier_timeout(None, 1.0) == native.MF_ERR_ARG
     assert lib.mf_film_solve_gradient(None, 1, None, None, None, 1, None, None, None, None, 0, None,
-                                      None, 0, None, None) == native.MF_ERR_ARG
+                                      None, 0, None, None, None) == native.MF_ERR_ARG
     one = (ctypes.c_int * 1)(64)
     out = (ctypes.c_int * 1)()
     assert lib.mf_batch_plan(-1, one, one, one, None, 304, out, out, out) == -1
