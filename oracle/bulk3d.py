@@ -45,7 +45,8 @@ class BulkProblem:
     def __init__(self, nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float,
                  mask: np.ndarray, *, n: float, rho_out: float, waveform: Waveform,
                  he_dir=(0.0, 0.0, 1.0), jc=1.0, e0: float = 1.0, sigma: float = 0.0,
-                 iter_tol: float = 1e-4, iter_max: int = 100):
+                 iter_tol: float = 1e-4, iter_max: int = 100, gamma: float = 1.0,
+                 b0: float = math.inf):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.L = (Lx, Ly, Lz)
         self.d = (2 * Lx / nx, 2 * Ly / ny, 2 * Lz / nz)
@@ -57,6 +58,8 @@ class BulkProblem:
         self.jc = np.broadcast_to(np.asarray(jc, dtype=np.float64), (nz, ny, nx))
         self.sigma = sigma if sigma > 0 else math.sqrt(sum(x * x for x in self.d))
         self.iter_tol, self.iter_max = float(iter_tol), int(iter_max)
+        self.gamma = float(gamma)          # anisotropy: the critical current along z is gamma jc
+        self.b0 = float(b0)                # field dependence jc / (1 + |h|/b0); inf: none
         self.wf = waveform
         self.he_dir = np.asarray(he_dir, dtype=np.float64)
 
@@ -100,16 +103,26 @@ class BulkProblem:
         return self._ifft_re([f * (ky * a[2] - kz * a[1]), f * (kz * a[0] - kx * a[2]),
                               f * (kx * a[1] - ky * a[0])])
 
-    def electric_field(self, j: np.ndarray) -> np.ndarray:
-        """Eq. 13 in the superconductor, Ohm law rho_out j elsewhere."""
-        jabs = np.sqrt((j * j).sum(axis=0))
-        rho_sc = (self.e0 / self.jc) * (jabs / self.jc) ** (self.n - 1.0)
+    def electric_field(self, j: np.ndarray, h: np.ndarray | None = None) -> np.ndarray:
+        """Eq. 13 in the superconductor, Ohm law rho_out j elsewhere.  Other laws of the same
+        family, which the paper's conclusion names as replacements: with gamma != 1 the
+        elliptic power law j_eff = sqrt(j_x^2 + j_y^2 + (j_z/gamma)^2),
+        e = rho(j_eff) (j_x, j_y, j_z/gamma^2); with a finite b0 the Kim-type critical current
+        jc / (1 + |h|/b0), |h| the local field (the state h at the cell)."""
+        g2 = self.gamma * self.gamma
+        jeff = np.sqrt(j[0] ** 2 + j[1] ** 2 + j[2] ** 2 / g2)
+        jc = self.jc
+        if math.isfinite(self.b0):
+            jc = jc / (1.0 + np.sqrt((np.asarray(h) ** 2).sum(axis=0)) / self.b0)
+        rho_sc = (self.e0 / jc) * (jeff / jc) ** (self.n - 1.0)
         rho = np.where(self.sc, rho_sc, self.rho_out)
-        return rho[None] * j
+        e = rho[None] * j
+        e[2] = e[2] * np.where(self.sc, 1.0 / g2, 1.0)
+        return e
 
     def hdot_in(self, h: np.ndarray) -> np.ndarray:
         """Eq. 14: h_dot = -curl e on the conductor, with e from j = curl h."""
-        e = self.electric_field(self.curl(h))
+        e = self.electric_field(self.curl(h), h)
         return np.where(self.conductor[None], -self.curl(e), 0.0)
 
     # ---- the right-hand side -------------------------------------------------------------

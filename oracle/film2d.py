@@ -63,7 +63,7 @@ class FilmProblem:
     def __init__(self, nx: int, ny: int, Lx: float, Ly: float, mask: np.ndarray, *, n: float,
                  rho_out: float, waveform: Waveform, jc=1.0, e0: float = 1.0,
                  sigma: float = 0.0, lam: float = 0.7, iter_tol: float = 2e-4,
-                 iter_max: int = 100):
+                 iter_max: int = 100, gamma: float = 1.0):
         self.nx, self.ny, self.Lx, self.Ly = nx, ny, Lx, Ly
         self.dx, self.dy = 2.0 * Lx / nx, 2.0 * Ly / ny
         self.mask = np.asarray(mask, dtype=np.uint8).reshape(ny, nx)
@@ -74,6 +74,7 @@ class FilmProblem:
         self.jc = np.broadcast_to(np.asarray(jc, dtype=np.float64), (ny, nx))
         self.sigma = sigma if sigma > 0 else math.sqrt(self.dx ** 2 + self.dy ** 2)
         self.lam, self.iter_tol, self.iter_max = float(lam), float(iter_tol), int(iter_max)
+        self.gamma = float(gamma)          # anisotropy: the critical current along y is gamma jc
         self.wf = waveform
 
         kx, nyq_x = wavenumbers(nx, Lx)
@@ -111,11 +112,15 @@ class FilmProblem:
         return gy, -gx
 
     def electric_field(self, jx: np.ndarray, jy: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
-        """Eq. 3 in the film, Ohm law rho_out j on free space and filled holes."""
-        jabs = np.sqrt(jx * jx + jy * jy)
-        rho_sc = (self.e0 / self.jc) * (jabs / self.jc) ** (self.n - 1.0)
+        """Eq. 3 in the film, Ohm law rho_out j on free space and filled holes.  With gamma != 1
+        the anisotropic (elliptic) law of the same family, one of the replacements the paper's
+        conclusion names: j_eff = sqrt(j_x^2 + (j_y/gamma)^2), rho = (e0/jc)|j_eff/jc|^(n-1),
+        e = rho (j_x, j_y/gamma^2) in the film (the critical current along y is gamma jc)."""
+        g2 = self.gamma * self.gamma
+        jeff = np.sqrt(jx * jx + jy * jy / g2)
+        rho_sc = (self.e0 / self.jc) * (jeff / self.jc) ** (self.n - 1.0)
         rho = np.where(self.sc, rho_sc, self.rho_out)
-        return rho * jx, rho * jy
+        return rho * jx, rho * jy * np.where(self.sc, 1.0 / g2, 1.0)
 
     def hdot_in(self, g: np.ndarray) -> np.ndarray:
         """Eq. 4 / Eq. 9: h_z_dot = -(d_x e_y - d_y e_x) on the conductor, 0 elsewhere."""

@@ -205,14 +205,14 @@ class FilmK2LambdaOne(FilmProblem):
 
 
 class BulkJcBaseDropped(BulkProblem):
-    def electric_field(self, j):
+    def electric_field(self, j, h=None):
         jabs = np.sqrt((j * j).sum(axis=0))
         rho = np.where(self.sc, (self.e0 / self.jc) * jabs ** (self.n - 1.0), self.rho_out)
         return rho[None] * j
 
 
 class BulkE0Dropped(BulkProblem):
-    def electric_field(self, j):
+    def electric_field(self, j, h=None):
         jabs = np.sqrt((j * j).sum(axis=0))
         rho = np.where(self.sc, (1.0 / self.jc) * (jabs / self.jc) ** (self.n - 1.0), self.rho_out)
         return rho[None] * j
