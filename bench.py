@@ -190,30 +190,49 @@ def autotune_leg(native, W, torch, n_grid: int):
             "timing": "CUDA events, 5 launches of one right-hand side with 4 forced outside iterations"}
 
 
-def adjoint_leg(native, W, torch, n_steps: int = 400, ckpt: int = 20, T: float = 0.1):
+def _adaptive_decisions(log):
+    """Accepted steps and per-step counts (k1, k2, k3) from a step log (k1 reused from the
+    previous step's k4 when the log shows it was not evaluated)."""
+    steps, counts, k4_prev = [], [], None
+    for (t, h, _tn, outcome, iters, _err) in log:
+        if outcome != 1:
+            continue
+        k1 = iters[0] if iters[0] >= 0 else k4_prev
+        steps.append((t, h))
+        counts += [int(k1), int(iters[1]), int(iters[2])]
+        k4_prev = iters[3]
+    return steps, counts
+
+
+def adjoint_leg(native, W, torch, T: float = 0.04, ckpt: int = 20):
     """Secondary line: the gradient of the film-solve loss on the gradient workload (512^2 film
-    in a 1024^2 grid, n = 30, lognormal jc map, 16 h_e knots on [0, T], n_steps frozen steps,
-    a checkpoint every `ckpt` steps), FP32 transforms, against the same frozen forward alone and
-    the plain FP64 forward.  The outside-iteration counts per call are the oracle's stop-test
-    counts stored in tests/golden (2 per call when the file is absent).  Target: h_z(T) of the
-    same frozen map with the second jc map (seed 6).  The calls are host-ordered launches;
-    timed with the host clock around each call (each waits for its stream)."""
+    in a 1024^2 grid, n = 30, lognormal jc map, 16 h_e knots on [0, T], a checkpoint every `ckpt`
+    steps), FP32 transforms, against the same frozen forward alone and the plain FP64 forward and
+    gradient.  The frozen decisions (accepted steps and per-call counts) are the oracle's adaptive
+    run stored in tests/golden, else this GPU's own adaptive run.  Target: h_z(T) of the same
+    frozen map with the second jc map (seed 6).  The calls are host-ordered launches, timed with
+    the host clock around each call (each waits for its stream)."""
     import numpy as np
     wl = W.adjoint_film(1024, precision=1, T=T)
-    steps = W.segment_steps(wl.he_knots[0], n_steps)
     path = os.path.join(ROOT, "tests", "golden", f"adjoint_{wl.name}.json")
-    iters, source = [2] * (3 * n_steps), "2 per call"
+    source = None
     if os.path.exists(path):
         ref = json.load(open(path))
-        if ref["steps"] == n_steps and abs(ref["T"] - T) < 1e-15:
-            iters, source = ref["counts"], "the oracle's stop-test counts (tests/golden)"
+        if abs(ref["T"] - T) < 1e-15:
+            steps, iters = [tuple(x) for x in ref["steps"]], ref["counts"]
+            source = "the oracle's adaptive run (tests/golden)"
+    if source is None:
+        pa = native.from_workload(wl)
+        pa.mf_advance(T)
+        steps, iters = _adaptive_decisions(pa.mf_get_log())
+        source = "this GPU's adaptive FP32 run"
     g0 = torch.zeros((wl.ny, wl.nx), dtype=torch.float64, device="cuda")
     zero = torch.zeros_like(g0)
     target = torch.zeros_like(g0)
     p6 = native.from_workload(wl, jc_map=W.jc_map_lognormal((wl.ny, wl.nx), seed=6, sigma=0.2))
     p6.mf_film_solve_gradient(g0, zero, steps, iters, ckpt, grad=False, hz_out=target)
-    out = {"workload": wl.name, "steps": n_steps, "T": T, "ckpt_every": ckpt, "counts": source,
-           "mean_iterations_per_call": float(np.mean(iters))}
+    out = {"workload": wl.name, "steps": len(steps), "T": T, "ckpt_every": ckpt,
+           "decisions": source, "mean_iterations_per_call": float(np.mean(iters))}
     for prec in (1, 0):
         wl.precision = prec
         p = native.from_workload(wl)
