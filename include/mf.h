@@ -75,6 +75,17 @@ typedef struct {
   int he_knots;               /* 0: use the sinusoid below */
   double he_sin_amp, he_sin_period;   /* h_e = amp sin(2 pi t / period) */
   double he_dir[3];           /* bulk: direction of the uniform applied field (default z) */
+  /* Other current-voltage laws of the same method (the conclusion of the paper names
+     anisotropic and field-dependent relations as drop-in replacements for Eq. 3 / Eq. 13).
+     Both act in the superconductor (mask 1) only; the defaults give Eq. 3 / Eq. 13. */
+  double gamma;               /* anisotropy > 0 (default 1): the elliptic power law
+                                 e = rho(j_eff) A j,  rho(s) = (e0/jc) (s/jc)^(n-1),
+                                 j_eff^2 = j^T A j,  A = diag(1, 1/gamma^2) for a film (the
+                                 critical current along y is gamma jc) and
+                                 diag(1, 1, 1/gamma^2) for a bulk body (along z) */
+  double b0;                  /* bulk only: > 0 gives the Kim-type critical current
+                                 jc / (1 + |h| / b0), |h| the local field of the state;
+                                 0 (default): none.  A film with b0 > 0 is MF_ERR_ARG. */
 } mf_params;
 
 /* One attempted BS23 step (lock-step log). */
@@ -98,7 +109,7 @@ typedef struct {
 enum { MF_READ_HZ = 0, MF_READ_MOMENT = 1, MF_READ_J = 2, MF_READ_E = 3 };
 
 /* Defaults: dim 2, n 19, jc = e0 = 1, rho_out 1, lambda 0.7, iter_tol 2e-4, iter_max 1000,
-   precision 0, rtol = atol = 1e-6, h_min 1e-12, he_dir (0,0,1). */
+   precision 0, rtol = atol = 1e-6, h_min 1e-12, he_dir (0,0,1), gamma 1, b0 0. */
 void mf_default_params(mf_params* p);
 
 /* Device workspace needed by mf_create for these parameters (0 if they are invalid). */

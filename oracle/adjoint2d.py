@@ -25,7 +25,8 @@ Derivative pieces (reverse order of the forward):
   * the warm start enters the first shift on free space, and the last iterate leaves the call:
     their cotangents are carried backwards from call to call;
   * Eq. 3: de/dj = rho (I + (n-1) j^ j^T) in the film, rho_out I elsewhere;
-    de/djc = -(n/jc) e in the film;
+    de/djc = -(n/jc) e in the film; for the elliptic law e = rho(s) A j, s^2 = j^T A j,
+    A = diag(1, 1/gamma^2) (FilmProblem's gamma): de/dj = rho (A + (n-1) (A j)(A j)^T / s^2);
   * the Runge-Kutta stages in reverse, each through the right-hand side's vector-Jacobian
     product; h_e_dot -> knot values through the segment slope, h_e(T) through the interpolation
     weights.
@@ -129,29 +130,31 @@ class FilmAdjoint:
         `warm` with `iters` outside iterations.  Returns (g_dot, last iterate, tape)."""
         p = self.p
         jx, jy = self.T(p.Dy, g), -self.T(p.Dx, g)               # Eq. 2
-        jabs = np.sqrt(jx * jx + jy * jy)
+        a = np.where(p.sc, 1.0 / (p.gamma * p.gamma), 1.0)       # A = diag(1, a)
+        jabs = np.sqrt(jx * jx + a * jy * jy)                    # s = |j|_A
         rho_sc = (p.e0 / jc) * (jabs / jc) ** (p.n - 1.0)        # Eq. 3
         rho = np.where(p.sc, rho_sc, p.rho_out)
-        ex, ey = rho * jx, rho * jy
+        ex, ey = rho * jx, rho * a * jy
         hin = np.where(self.cond, -(self.T(p.Dx, ey) - self.T(p.Dy, ex)), 0.0)   # Eq. 4 / 9
         gd, last = self.P_warm(hin, s, warm, iters)
-        return gd, last, (jx, jy, jabs, rho, ex, ey)
+        return gd, last, (jx, jy, jabs, rho, ex, ey, a)
 
     def call_vjp(self, tape, jc, iters, v, wbar):
         """(adjoint of g, of the jc map, of h_e_dot, of the warm start) of one call for the
         cotangents v of its g_dot and wbar of its last iterate (None: 0)."""
         p = self.p
-        jx, jy, jabs, rho, ex, ey = tape
+        jx, jy, jabs, rho, ex, ey, a = tape
         hbar_in, sbar, warm_bar = self.P_T_warm(v, wbar, iters)
         rbar = np.where(self.cond, -hbar_in, 0.0)                # h_in = -raw on the conductor
         eybar = self.Tt(p.Dx, rbar)                              # raw = Dx e_y - Dy e_x
         exbar = -self.Tt(p.Dy, rbar)
         safe = np.where(jabs > 0, jabs, 1.0)
-        ux, uy = np.where(jabs > 0, jx / safe, 0.0), np.where(jabs > 0, jy / safe, 0.0)
+        # unit vector A j / s
+        ux, uy = np.where(jabs > 0, jx / safe, 0.0), np.where(jabs > 0, a * jy / safe, 0.0)
         proj = ux * exbar + uy * eybar
         nn = np.where(p.sc, p.n - 1.0, 0.0)                      # Ohm's law elsewhere
         jxbar = rho * (exbar + nn * ux * proj)
-        jybar = rho * (eybar + nn * uy * proj)
+        jybar = rho * (a * eybar + nn * uy * proj)
         jcbar = np.where(p.sc, -(p.n / jc) * (exbar * ex + eybar * ey), 0.0)
         gbar = self.Tt(p.Dy, jxbar) - self.Tt(p.Dx, jybar)       # j_x = Dy g, j_y = -Dx g
         return gbar, jcbar, sbar, warm_bar

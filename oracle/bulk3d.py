@@ -26,7 +26,10 @@ Arrays are (3, nz, ny, nx), component-major (SoA).  Pinned by tests/test_oracle_
 curl of trig fields, the closed-form centre field (2/3) m0 of a spherically symmetric Gaussian
 magnetization for Phi, curl Phi[j] = j for divergence-free j, Ohmic linearity, invariants and
 the Bean slab profile; by tests/test_oracle_power_law_pins.py: the exact jc and e0 scalings of
-Eq. 13 with a lognormal jc map.
+Eq. 13 with a lognormal jc map; by tests/test_oracle_laws.py: the elliptic law (gamma) through
+the gamma^2-slower Ohmic decay of a mode whose current runs along z and the critical current
+gamma jc of a slab carrying it, and the Kim law (b0) through |j| (1 + |h|/b0) = jc across a fully
+penetrated slab.
 """
 from __future__ import annotations
 

@@ -37,7 +37,9 @@ eddy-current mode of an unbounded Ohmic sheet, and Bean-limit flux fronts of a s
 tests/test_oracle_power_law_pins.py: the exact jc and e0 scalings of Eq. 3 with a lognormal jc
 map, the Bean strip with a non-uniform jc (|j| = local jc in the penetrated zones), and Eq. 12's
 multiplier as lambda times the smoothed field of the stray current; by
-tests/test_oracle_direct_sums.py: every multiplier against O(N^2) Fourier sums.
+tests/test_oracle_direct_sums.py: every multiplier against O(N^2) Fourier sums; by
+tests/test_oracle_laws.py: the elliptic law (gamma) through the gamma^2-slower Ohmic decay of a
+mode whose current runs along y and the critical sheet current gamma jc of a strip along y.
 """
 from __future__ import annotations
 

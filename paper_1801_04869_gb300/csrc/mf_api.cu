@@ -90,6 +90,9 @@ mf_status check_params(const mf_params* p, std::string& why) {
     if (!(p->he_t[i] > p->he_t[i - 1])) { why = "h_e knot times must increase"; return MF_ERR_ARG; }
   if (p->he_knots == 0 && !(p->he_sin_period > 0)) { why = "sinusoid period must be positive"; return MF_ERR_ARG; }
   if (!(p->rtol >= 0) || !(p->atol > 0)) { why = "need rtol >= 0 and atol > 0"; return MF_ERR_ARG; }
+  if (!(p->gamma > 0) || !std::isfinite(p->gamma)) { why = "gamma must be positive and finite"; return MF_ERR_ARG; }
+  if (!(p->b0 >= 0) || !std::isfinite(p->b0)) { why = "b0 must be >= 0 and finite"; return MF_ERR_ARG; }
+  if (p->dim == 2 && p->b0 > 0) { why = "the field-dependent jc (b0 > 0) is a bulk law"; return MF_ERR_ARG; }
   return MF_OK;
 }
 
@@ -232,6 +235,7 @@ void mf_default_params(mf_params* p) {
   p->rtol = 1e-6; p->atol = 1e-6; p->h0 = 0.0; p->h_min = 1e-12;
   p->he_sin_amp = 0.0; p->he_sin_period = 1.0;
   p->he_dir[0] = 0.0; p->he_dir[1] = 0.0; p->he_dir[2] = 1.0;
+  p->gamma = 1.0; p->b0 = 0.0;
 }
 
 size_t mf_workspace_bytes(const mf_params* p) {
@@ -268,6 +272,7 @@ mf_status mf_create(const mf_params* p, void* d_workspace, size_t bytes, void* s
   const double s2 = d.dx * d.dx + d.dy * d.dy + d.dz * d.dz;
   d.sigma = p->sigma > 0 ? p->sigma : std::sqrt(s2);   // Section 2.2 / Section 3.2 choice
   d.n = p->n; d.e0 = p->e0; d.jc = p->jc; d.rho_out = p->rho_out; d.lam = p->lambda;
+  d.gamma = p->gamma; d.b0 = p->b0;
   d.iter_tol = p->iter_tol; d.iter_max = p->iter_max;
   d.barrier_ns = BARRIER_LIMIT_NS;
   d.rtol = p->rtol; d.atol = p->atol; d.h_min = p->h_min;

@@ -286,11 +286,17 @@ struct Bulk {
 // ------------------------------------------------------------------------------------------
 // epilogues of the x pass (cell index i, three components in / out)
 // ------------------------------------------------------------------------------------------
+// Stage state y + sum c_j k_j.  With a field-dependent critical current (kim) the stage
+// field's magnitude |h| is kept, in the transform precision, in the first component of the
+// h_dot iterate at superconductor cells: those entries are rewritten by BInit before anything
+// reads them as an iterate, and the warm start lives on free space only.
 template <typename T>
 struct BStage : EpiBase<T> {
   BulkPtrs<T> P;
   StageIn in;
+  bool kim;
   __device__ void operator()(long long i, const T*, T* out) {
+    double h2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long k = c * P.ncell + i;
@@ -298,19 +304,31 @@ struct BStage : EpiBase<T> {
       for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][k];
       if (in.ynew) in.ynew[k] = v;
       out[c] = (T)v;
+      h2 += v * v;
     }
+    if (kim && __ldg(&P.mask[i]) == 1) P.hd[i] = (T)sqrt(h2);
   }
 };
 
+// local law of the superconductor: critical current (Kim-type jc / (1 + |h|/b0) when ib0 > 0,
+// |h| left by BStage) and the elliptic weight a = 1/gamma^2 of j_z
 template <typename T>
-struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law)
+__device__ __forceinline__ T bulk_jc(const BulkPtrs<T>& P, long long i, int m, T jc, T ib0) {
+  T jcl = P.jcmap ? __ldg(&P.jcmap[i]) : jc;
+  if (ib0 > (T)0 && m == 1) jcl = jcl / ((T)1 + P.hd[i] * ib0);
+  return jcl;
+}
+
+template <typename T>
+struct BPower : EpiBase<T> {               // j -> e (Eq. 13 / Ohm law; elliptic and Kim laws)
   BulkPtrs<T> P;
-  T n, e0, jc, rho_out;
+  T n, e0, jc, rho_out, ig2, ib0;
   __device__ void operator()(long long i, const T* in, T* out) {
     const int m = __ldg(&P.mask[i]);
-    const T jcl = P.jcmap ? __ldg(&P.jcmap[i]) : jc;
-    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
-    out[0] = rho * in[0]; out[1] = rho * in[1]; out[2] = rho * in[2];
+    const T jcl = bulk_jc(P, i, m, jc, ib0);
+    const T a = m == 1 ? ig2 : (T)1;
+    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2] * a, jcl, m, n, e0, rho_out);
+    out[0] = rho * in[0]; out[1] = rho * in[1]; out[2] = rho * in[2] * a;
   }
 };
 
@@ -403,15 +421,16 @@ struct BStoreJ : EpiBase<T> {              // readout of j = curl h (FP64)
 };
 
 template <typename T>
-struct BStoreE : EpiBase<T> {              // readout of e = rho(|j|) j (Eq. 13 / Ohm law, FP64)
+struct BStoreE : EpiBase<T> {              // readout of e, the law of BPower (FP64)
   BulkPtrs<T> P;
-  T n, e0, jc, rho_out;
+  T n, e0, jc, rho_out, ig2, ib0;
   double* out;
   __device__ void operator()(long long i, const T* in, T*) {
     const int m = __ldg(&P.mask[i]);
-    const T jcl = P.jcmap ? __ldg(&P.jcmap[i]) : jc;
-    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2], jcl, m, n, e0, rho_out);
-    out[i] = rho * in[0]; out[P.ncell + i] = rho * in[1]; out[2 * P.ncell + i] = rho * in[2];
+    const T jcl = bulk_jc(P, i, m, jc, ib0);
+    const T a = m == 1 ? ig2 : (T)1;
+    const T rho = resistivity<T>(in[0] * in[0] + in[1] * in[1] + in[2] * in[2] * a, jcl, m, n, e0, rho_out);
+    out[i] = rho * in[0]; out[P.ncell + i] = rho * in[1]; out[2 * P.ncell + i] = rho * in[2] * a;
   }
 };
 
@@ -448,11 +467,12 @@ __device__ __noinline__ RhsOut bulk_rhs(Bulk<T>& B, double t, int seg, const Sta
   const double hed_norm = sqrt(hed[0] * hed[0] + hed[1] * hed[1] + hed[2] * hed[2]);
 #define BSYNC(w) if (!B.sync(w)) { res.status = ST_BARRIER; return res; }
 #define BYZY(op, w) if (!B.yzy(op, w)) { res.status = ST_BARRIER; return res; }
-  { BStage<T> e; e.P = B.ptrs(); e.in = sin; B.xpass<0, 3>(e, -1); }
+  { BStage<T> e; e.P = B.ptrs(); e.in = sin; e.kim = d.b0 > 0.0; B.xpass<0, 3>(e, -1); }
   BSYNC(101);
   BYZY(OP3_CURL, 102);                                                   // j = curl h
   {
     BPower<T> e; e.P = B.ptrs(); e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+    e.ig2 = (T)(1.0 / (d.gamma * d.gamma)); e.ib0 = d.b0 > 0.0 ? (T)(1.0 / d.b0) : (T)0;
     B.xpass<3, 3>(e, -1);                                                // e = rho j
   }
   BSYNC(105);
@@ -548,7 +568,7 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(const Desc* __restrict__ dg
     if (leader) { st->last_iters = r.iters; st->last_r = r.r; st->n_rhs += 1; st->n_iters += r.iters; }
   } else if (a.mode == MODE_J || a.mode == MODE_E || a.mode == MODE_MOMENT) {
     StageIn in{a.y_in, 0, {0, 0, 0}, {nullptr, nullptr, nullptr}, nullptr};
-    { BStage<T> e; e.P = B.ptrs(); e.in = in; B.xpass<0, 3>(e, -1); }
+    { BStage<T> e; e.P = B.ptrs(); e.in = in; e.kim = a.mode == MODE_E && d.b0 > 0.0; B.xpass<0, 3>(e, -1); }
     bool ok = B.sync(201) && B.yzy(OP3_CURL, 202);
     if (ok) {
       if (a.mode == MODE_J) {
@@ -557,6 +577,7 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(const Desc* __restrict__ dg
       } else if (a.mode == MODE_E) {
         BStoreE<T> e; e.P = B.ptrs(); e.out = a.out;
         e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+        e.ig2 = (T)(1.0 / (d.gamma * d.gamma)); e.ib0 = d.b0 > 0.0 ? (T)(1.0 / d.b0) : (T)0;
         B.xpass<3, 0>(e, -1);
       } else {
         for (int c = 0; c < 3 && ok; ++c) {

@@ -135,6 +135,7 @@ struct Desc {
   int lgx, lgy, lgz;
   double Lx, Ly, Lz, dx, dy, dz;
   double n, e0, jc, rho_out, sigma, lam, iter_tol;
+  double gamma, b0;              // elliptic anisotropy (1: isotropic); Kim field scale (0: none)
   int iter_max;
   double rtol, atol, h_min;
   // applied field

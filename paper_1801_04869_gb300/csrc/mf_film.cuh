@@ -433,11 +433,13 @@ struct EpiStoreHz : EpiBase<T> {
   }
 };
 
-// P3: power law
+// P3: power law.  ig2 = 1/gamma^2 of the elliptic law e = rho(j_eff) (j_x, j_y/gamma^2),
+// j_eff^2 = j_x^2 + j_y^2/gamma^2 in the superconductor (Eq. 3 at gamma = 1, where the extra
+// products by 1 are exact)
 template <typename T>
 struct EpiPower : EpiBase<T> {
   FilmPtrs<T> P;
-  T n, e0, jc, rho_out;
+  T n, e0, jc, rho_out, ig2;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     V4<T> jcl;
@@ -447,9 +449,11 @@ struct EpiPower : EpiBase<T> {
     for (int q = 0; q < 4; ++q) {
       const T gx = in[0].v[q], gy = in[1].v[q];
       const T jx = gy, jy = -gx;                              // Eq. 2
-      const T rho = resistivity<T>(jx * jx + jy * jy, jcl.v[q], mask_at(m, q), n, e0, rho_out);
+      const int mq = mask_at(m, q);
+      const T a = mq == 1 ? ig2 : (T)1;
+      const T rho = resistivity<T>(jx * jx + jy * jy * a, jcl.v[q], mq, n, e0, rho_out);
       out[0].v[q] = rho * jx;                                 // Eq. 3
-      out[1].v[q] = rho * jy;
+      out[1].v[q] = rho * jy * a;
     }
   }
 };
@@ -565,7 +569,7 @@ struct EpiFinal : EpiBase<T> {
 template <typename T>
 struct EpiStoreE : EpiBase<T> {
   FilmPtrs<T> P;
-  T n, e0, jc, rho_out;
+  T n, e0, jc, rho_out, ig2;
   double* dst;
   long long ncell;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>*) {
@@ -577,9 +581,11 @@ struct EpiStoreE : EpiBase<T> {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T jx = in[1].v[q], jy = -in[0].v[q];
-      const T rho = resistivity<T>(jx * jx + jy * jy, jcl.v[q], mask_at(m, q), n, e0, rho_out);
+      const int mq = mask_at(m, q);
+      const T a = mq == 1 ? ig2 : (T)1;                       // elliptic law, as in EpiPower
+      const T rho = resistivity<T>(jx * jx + jy * jy * a, jcl.v[q], mq, n, e0, rho_out);
       ex.v[q] = (double)(rho * jx);
-      ey.v[q] = (double)(rho * jy);
+      ey.v[q] = (double)(rho * jy * a);
     }
     st4(dst + i, ex);
     st4(dst + ncell + i, ey);
@@ -626,6 +632,7 @@ __device__ __noinline__ RhsOut film_rhs(Film<T>& F, double t, int seg, const Sta
   {
     EpiPower<T> e; e.P = F.ptrs();
     e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+    e.ig2 = (T)(1.0 / (d.gamma * d.gamma));
     F.rows<2, 2>(F.rb2, F.Sa, F.Sb, e, -1);                             // P3
   }
   if (!F.sync(3)) { res.status = ST_BARRIER; return res; }
@@ -788,6 +795,7 @@ __device__ __forceinline__ void film_main(const Desc& d, const KernelArgs& a, in
       if (F.sync(51)) {
         EpiStoreE<T> es; es.P = F.ptrs(); es.dst = a.out; es.ncell = F.ncell;
         es.n = (T)d.n; es.e0 = (T)d.e0; es.jc = (T)d.jc; es.rho_out = (T)d.rho_out;
+        es.ig2 = (T)(1.0 / (d.gamma * d.gamma));
         F.rows<2, 0>(F.rb2, F.Sa, nullptr, es, -1);
       } else status = ST_BARRIER;
     } else status = ST_BARRIER;

@@ -102,14 +102,17 @@ struct EpiRbar : EpiBase<T, T> {
   }
 };
 
-// full product: ebar = (d_y r, -d_x r); linearised power law -> jbar (forward), jcbar
+// full product: ebar = (d_y r, -d_x r); linearised power law -> jbar (forward), jcbar.
+// Elliptic law e = rho(s) A j, s^2 = j^T A j, A = diag(1, a), a = 1/gamma^2 in the
+// superconductor: jbar = rho A ebar + (n-1) rho (A j)(A j . ebar) / s^2 and
+// jcbar = -(n/jc) rho (A j . ebar) (rho scales as jc^-n at fixed j)
 template <typename T>
 struct EpiPowVJP : EpiBase<T, T> {
   FilmPtrs<T> P;
   const T* jx;
   const T* jy;
   double* jcbar;
-  T n, e0, jc, rho_out;
+  T n, e0, jc, rho_out, ig2;
   __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
     const uchar4 m = ldmask4(P.mask + i);
     V4<T> jcl;
@@ -121,20 +124,22 @@ struct EpiPowVJP : EpiBase<T, T> {
     for (int q = 0; q < 4; ++q) {
       const T ex = in[1].v[q], ey = -in[0].v[q];                 // transposed -curl
       const T x = ax.v[q], y = ay.v[q];
-      const T j2 = x * x + y * y;
       const int mq = mask_at(m, q);
+      const T a = mq == 1 ? ig2 : (T)1;
+      const T Ay = y * a;                                          // (A j)_y
+      const T j2 = x * x + y * Ay;
       const T rho = resistivity<T>(j2, jcl.v[q], mq, n, e0, rho_out);
-      T bx = rho * ex, by = rho * ey;
+      T bx = rho * ex, by = rho * ey * a;
       double c = 0.0;
       if (mq == 1) {
         if (j2 > (T)0) {
           const T inv = (T)1 / sqrt(j2);
-          const T ux = x * inv, uy = y * inv;
+          const T ux = x * inv, uy = Ay * inv;
           const T pr = (n - (T)1) * rho * (ux * ex + uy * ey);
           bx += pr * ux;
           by += pr * uy;
         }
-        c = -(double)(n / jcl.v[q]) * (double)(rho * (ex * x + ey * y));
+        c = -(double)(n / jcl.v[q]) * (double)(rho * (ex * x + ey * Ay));
       }
       out[0].v[q] = bx;
       out[1].v[q] = by;
@@ -315,6 +320,7 @@ __global__ void __launch_bounds__(NT, 2) film_adjoint_kernel(const Desc* __restr
         {
           EpiPowVJP<T> e; e.P = F.ptrs(); e.jx = jx; e.jy = jy; e.jcbar = a.jcbar;
           e.n = (T)d.n; e.e0 = (T)d.e0; e.jc = (T)d.jc; e.rho_out = (T)d.rho_out;
+          e.ig2 = (T)(1.0 / (d.gamma * d.gamma));
           F.rows<2, 2>(F.rb2, F.Sb, F.Sa, e, -1);                       // jbar, jcbar (Eq. 3)
         }
         if (!F.sync(64)) { status = ST_BARRIER; break; }

@@ -117,6 +117,7 @@ extern "C" mf_status mf_film_rhs_noalloc(const mf_params* p, double t, const dou
   d.dx = 2 * p->Lx / nx; d.dy = 2 * p->Ly / ny;
   d.sigma = p->sigma > 0 ? p->sigma : std::sqrt(d.dx * d.dx + d.dy * d.dy);
   d.n = p->n; d.e0 = p->e0; d.jc = p->jc; d.rho_out = p->rho_out; d.lam = p->lambda;
+  d.gamma = p->gamma; d.b0 = p->b0;
   d.iter_tol = p->iter_tol; d.iter_max = p->iter_max;
   d.rtol = p->rtol; d.atol = p->atol; d.h_min = p->h_min;
   d.he_knots = p->he_knots; d.he_sin_amp = p->he_sin_amp; d.he_sin_period = p->he_sin_period;

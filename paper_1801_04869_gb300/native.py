@@ -46,6 +46,7 @@ class mf_params(ctypes.Structure):
         ("he_t", ctypes.POINTER(ctypes.c_double)), ("he_v", ctypes.POINTER(ctypes.c_double)),
         ("he_knots", ctypes.c_int), ("he_sin_amp", ctypes.c_double),
         ("he_sin_period", ctypes.c_double), ("he_dir", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double), ("b0", ctypes.c_double),
     ]
 
 
@@ -153,7 +154,8 @@ class Problem:
                  jc: float = 1.0, jc_map=None, e0: float = 1.0, sigma: float = 0.0,
                  lam: float = 0.7, iter_tol: float = 2e-4, iter_max: int = 1000,
                  rtol: float = 1e-6, atol: float = 1e-6, h0: float = 0.0, h_min: float = 1e-12,
-                 he_knots=None, he_sin=None, he_dir=(0.0, 0.0, 1.0), device=None, stream=None):
+                 he_knots=None, he_sin=None, he_dir=(0.0, 0.0, 1.0), gamma: float = 1.0,
+                 b0: float = 0.0, device=None, stream=None):
         import torch
         lib = load()
         self.lib = lib
@@ -181,6 +183,7 @@ class Problem:
             amp, per = he_sin if he_sin is not None else (0.0, 1.0)
             p.he_knots, p.he_sin_amp, p.he_sin_period = 0, amp, per
         p.he_dir[0], p.he_dir[1], p.he_dir[2] = he_dir
+        p.gamma, p.b0 = gamma, b0
         self.params = p
         nbytes = lib.mf_workspace_bytes(ctypes.byref(p))
         if nbytes == 0:
@@ -434,6 +437,7 @@ def from_workload(wl, **over) -> Problem:
               mask=wl.mask, n=wl.n, rho_out=wl.rho_out, precision=wl.precision,
               jc=wl.jc, jc_map=wl.jc_map, sigma=wl.sigma, lam=wl.lam, iter_tol=wl.iter_tol,
               iter_max=wl.iter_max, rtol=wl.rtol, atol=wl.atol, he_knots=wl.he_knots,
-              he_sin=wl.he_sin, he_dir=wl.vector_he)
+              he_sin=wl.he_sin, he_dir=wl.vector_he, gamma=getattr(wl, "gamma", 1.0),
+              b0=getattr(wl, "b0", 0.0))
     kw.update(over)
     return Problem(**kw)

@@ -17,7 +17,10 @@ def waveform_of(wl: W.Workload) -> Waveform:
 
 def oracle_of(wl: W.Workload, **over):
     kw = dict(n=wl.n, rho_out=wl.rho_out, waveform=waveform_of(wl), jc=wl.jc if wl.jc_map is None
-              else wl.jc_map, sigma=wl.sigma, iter_tol=wl.iter_tol, iter_max=wl.iter_max)
+              else wl.jc_map, sigma=wl.sigma, iter_tol=wl.iter_tol, iter_max=wl.iter_max,
+              gamma=wl.gamma)
+    if wl.dim == 3 and wl.b0 > 0:
+        kw["b0"] = wl.b0
     if wl.dim == 2:
         kw["lam"] = wl.lam
         kw.update(over)

@@ -37,6 +37,31 @@ def test_struct_layouts_match_header(lib):
     p = native.mf_params()
     lib.mf_default_params(ctypes.byref(p))
     assert p.n == 19.0 and p.lambda_ == 0.7 and p.iter_tol == 2e-4 and p.he_dir[2] == 1.0
+    assert p.gamma == 1.0 and p.b0 == 0.0                 # the last fields: the tail's offsets
+
+
+def test_law_parameters_are_checked(lib):
+    import numpy as np
+    from paper_1801_04869_gb300 import native
+    p = native.mf_params()
+    lib.mf_default_params(ctypes.byref(p))
+    m = np.zeros(16 ** 3, np.uint8)
+    p.nx = p.ny = 16
+    p.Lx = p.Ly = 2.0
+    p.mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) > 0
+    for g in (0.0, -1.0, float("inf"), float("nan")):
+        p.gamma = g
+        assert lib.mf_workspace_bytes(ctypes.byref(p)) == 0, g
+    p.gamma = 2.0
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) > 0
+    p.b0 = 0.3                                              # Kim-type jc is a bulk law
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) == 0
+    p.dim, p.nz, p.Lz = 3, 16, 2.0
+    assert lib.mf_workspace_bytes(ctypes.byref(p)) > 0
+    for b in (-0.1, float("inf"), float("nan")):
+        p.b0 = b
+        assert lib.mf_workspace_bytes(ctypes.byref(p)) == 0, b
 
 
 def test_readout_enum_matches_header():

@@ -12,20 +12,22 @@ N, L = 32, 2.0
 KT, KV = [0.0, 0.5, 1.0], [0.0, 0.3, 0.45]
 
 
-def _setup(n_power=19.0, iters=4, seed=31, amplitude=1.6):
+def _setup(n_power=19.0, iters=4, seed=31, amplitude=1.6, gamma=1.0):
     # amplitude 1.6 on this grid puts |j| just below jc (the smoothing rounds the critical-state
     # slope), where the power law is sensitive to jc
     mask = W.film_mask(N, N, L, L, "rect", ax=1.0, ay=0.75)
     jc = W.jc_map_lognormal((N, N), seed=seed, sigma=0.05)
     p = FilmProblem(N, N, L, L, mask, n=n_power, rho_out=1.0, waveform=Waveform(KT, KV), jc=jc,
-                    iter_tol=0.0, iter_max=iters)
+                    iter_tol=0.0, iter_max=iters, gamma=gamma)
     g0 = W.film_state(mask, L, L, seed=seed, amplitude=amplitude)
     return p, FilmAdjoint(p, iters), g0, np.array(p.jc)
 
 
-def test_forward_rhs_equals_the_film_oracle():
-    """Cold start and a fixed iteration count: the adjoint's f is FilmProblem.rhs."""
-    p, a, g0, jc = _setup()
+@pytest.mark.parametrize("gamma", [1.0, 1.6])
+def test_forward_rhs_equals_the_film_oracle(gamma):
+    """Cold start and a fixed iteration count: the adjoint's f is FilmProblem.rhs (with the
+    elliptic law too)."""
+    p, a, g0, jc = _setup(gamma=gamma)
     s = p.wf.hedot(0.2)
     ref, it, _ = p.rhs(0.2, g0, None, a.I)
     got, _ = a.rhs(g0, jc, s)
@@ -49,8 +51,9 @@ def _fd(fun, x, d, eps):
     return (fun(x + eps * d) - fun(x - eps * d)) / (2 * eps)
 
 
-def test_rhs_vjp_matches_finite_differences():
-    p, a, g0, jc = _setup()
+@pytest.mark.parametrize("gamma", [1.0, 1.6])
+def test_rhs_vjp_matches_finite_differences(gamma):
+    p, a, g0, jc = _setup(gamma=gamma)
     r = W.rng(33)
     s = 0.3
     v = r.standard_normal((N, N))

@@ -178,6 +178,8 @@ class Workload:
     jc: float = 1.0
     jc_map: np.ndarray | None = None
     vector_he: tuple[float, float, float] = (0.0, 0.0, 1.0)
+    gamma: float = 1.0            # elliptic anisotropy of the law (film: along y, bulk: along z)
+    b0: float = 0.0               # bulk Kim-type jc / (1 + |h|/b0); 0: none
 
 
 def square_film_128(precision: int = 0) -> Workload:
