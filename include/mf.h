@@ -198,7 +198,8 @@ mf_status mf_step(mf_problem* pb, double t_max, int* accepted);
 /* Integrate from the current state to each time in t_out (increasing) and record readouts:
    h_m_out (host, may be NULL) gets the magnetization (film: m_z, 1 value per time; bulk:
    m, 3 values per time); d_hz_out (device, may be NULL) gets h_z (film) or j (bulk, 3 fields)
-   per output time. */
+   per output time.  An unset first step (mf_params.h0 <= 0, nothing integrated yet) is chosen
+   for the whole span up to the last output time: min(1e-3, 0.01 (t_out[n_out-1] - t)). */
 mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_m_out,
                       double* d_hz_out);
 

@@ -746,6 +746,12 @@ mf_status mf_run_ramp(mf_problem* pb, int n_out, const double* t_out, double* h_
   if (!pb || n_out < 0 || (n_out > 0 && !t_out)) return MF_ERR_ARG;
   const int nm = pb->d.dim == 2 ? 1 : 3;
   const long long per = pb->d.dim == 2 ? pb->d.ncell : 3 * pb->d.ncell;
+  if (n_out > 0) {
+    // an unset first step is chosen for the whole ramp [t, last output time], as for one
+    // advance to its end (an integrator given all output times at once sees the whole span)
+    mf_status r = ensure_h(pb, t_out[n_out - 1]);
+    if (r != MF_OK) return r;
+  }
   for (int k = 0; k < n_out; ++k) {
     mf_status r = mf_advance(pb, t_out[k], 1LL << 40);
     if (r != MF_OK) return r;

@@ -96,7 +96,9 @@ struct Bulk {
     const int lgpair = __ffs(npair) - 1;
     if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(sm, sm2, S1 + off, nspec, ny, npair, lgpair, lgx, twx);
     C2<T>* Y = X == sm ? sm2 : sm;
-#pragma unroll 2
+    // not unrolled: a second cell in flight spilled the epilogues' live values (26% slower
+    // per outside iteration on the 128^3 grid)
+#pragma unroll 1
     for (int e = threadIdx.x; e < (npair << lgx); e += NT) {
       const int pr = e >> lgx, x = e & (nx - 1);
       T ina[3], inb[3], oa[3], ob[3];

@@ -104,22 +104,44 @@ __device__ __forceinline__ void dft(C2<T>* v) {
   }
 }
 
-// Twiddles w^(j k), 1 <= j < R, of one butterfly: the entries j = 1, 2, 4, 8 come from the
-// stage's block of the stage-ordered table (entry (j - 1) p + k), the others are products of
-// two of them (w^(3k) = w^k w^(2k), ...), at most three roundings from the table values.
-// Conjugated for the inverse direction.
+// Twiddles w^(j k), 1 <= j < R, of one butterfly, applied in place (v[j] *= w^(j k)): the powers
+// j = 1, 2, 4, 8 come from the stage's block of the stage-ordered table (entry (j - 1) p + k;
+// twiddle_base loads them, conjugated for the inverse direction), the others are products of
+// two of them (w^(3k) = w^(2k) w^k, w^(7k) = w^(4k) w^(3k), ...), at most three roundings from
+// the table values.  Each product is formed next to its use, so only the base powers and four
+// odd products stay live (register pressure of the radix-16 stage).
 template <typename T, int R, int DIR>
-__device__ __forceinline__ void stage_twiddles(const C2<T>* __restrict__ twk, int p, C2<T>* w) {
+__device__ __forceinline__ void twiddle_base(const C2<T>* __restrict__ twk, int p, C2<T>* b) {
 #pragma unroll
-  for (int j = 1; j < R; j <<= 1) {
-    w[j] = ldg_c2(twk + (j - 1) * p);
-    if (DIR > 0) w[j].y = -w[j].y;
+  for (int j = 1, s = 0; j < R; j <<= 1, ++s) {
+    b[s] = ldg_c2(twk + (j - 1) * p);
+    if (DIR > 0) b[s].y = -b[s].y;
   }
-#pragma unroll
-  for (int j = 3; j < R; ++j) {
-    if ((j & (j - 1)) == 0) continue;
-    const int hb = j >= 8 ? 8 : (j >= 4 ? 4 : 2);          // highest power of two below j
-    w[j] = cmul(w[hb], w[j - hb]);
+}
+template <typename T, int R>
+__device__ __forceinline__ void twiddle_apply(const C2<T>* b, C2<T>* v) {
+  v[1] = cmul(v[1], b[0]);
+  if constexpr (R > 2) {
+    v[2] = cmul(v[2], b[1]);
+    const C2<T> w3 = cmul(b[1], b[0]);
+    v[3] = cmul(v[3], w3);
+    if constexpr (R > 4) {
+      v[4] = cmul(v[4], b[2]);
+      const C2<T> w5 = cmul(b[2], b[0]), w6 = cmul(b[2], b[1]), w7 = cmul(b[2], w3);
+      v[5] = cmul(v[5], w5);
+      v[6] = cmul(v[6], w6);
+      v[7] = cmul(v[7], w7);
+      if constexpr (R > 8) {
+        v[8] = cmul(v[8], b[3]);
+        v[9] = cmul(v[9], cmul(b[3], b[0]));
+        v[10] = cmul(v[10], cmul(b[3], b[1]));
+        v[11] = cmul(v[11], cmul(b[3], w3));
+        v[12] = cmul(v[12], cmul(b[3], b[2]));
+        v[13] = cmul(v[13], cmul(b[3], w5));
+        v[14] = cmul(v[14], cmul(b[3], w6));
+        v[15] = cmul(v[15], cmul(b[3], w7));
+      }
+    }
   }
 }
 
@@ -158,10 +180,9 @@ __device__ __forceinline__ void fft_stage(const C2<T>* in_p, C2<T>* out_p, int l
       for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
     }
     if (lgp > 0) {
-      C2<T> w[R];
-      stage_twiddles<T, R, DIR>(tw + k, p, w);
-#pragma unroll
-      for (int j = 1; j < R; ++j) v[j] = cmul(v[j], w[j]);
+      C2<T> wb[LGR];
+      twiddle_base<T, R, DIR>(tw + k, p, wb);
+      twiddle_apply<T, R>(wb, v);
     }
     dft<T, R, DIR>(v);
     const int dst = (line << lgL) + ((i - k) << LGR) + k;
@@ -311,10 +332,9 @@ __device__ __forceinline__ void fft_last_io(const C2<T>* in_p, int lgL, int lgp,
       for (int j = 0; j < R; ++j) v[j] = S[in + sp(src + (j << lgq))];
     }
     if (lgp > 0) {
-      C2<T> w[R];
-      stage_twiddles<T, R, DIR>(tw + k, p, w);
-#pragma unroll
-      for (int j = 1; j < R; ++j) v[j] = cmul(v[j], w[j]);
+      C2<T> wb[LGR];
+      twiddle_base<T, R, DIR>(tw + k, p, wb);
+      twiddle_apply<T, R>(wb, v);
     }
     dft<T, R, DIR>(v);
     const int dpos = ((i - k) << LGR) + k;
@@ -360,8 +380,8 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int 
     const int l = b >> lgq, i = b & (q - 1);
     C2<T> x[NFI][R];
     // twiddles of the last forward stage (p = q, k = i), from its block of the table
-    C2<T> w[R];
-    stage_twiddles<T, R, -1>(tw + i, q, w);
+    C2<T> wb[LGR];
+    twiddle_base<T, R, -1>(tw + i, q, wb);
 #pragma unroll
     for (int f = 0; f < NFI; ++f) {
       const int base = ((f * nl + l) << lgL) + i;
@@ -373,8 +393,7 @@ __device__ __forceinline__ void fft_middle(const C2<T>* in_p, C2<T>* out_p, int 
 #pragma unroll
         for (int j = 0; j < R; ++j) x[f][j] = S[in + sp(base + (j << lgq))];
       }
-#pragma unroll
-      for (int j = 1; j < R; ++j) x[f][j] = cmul(x[f][j], w[j]);
+      twiddle_apply<T, R>(wb, x[f]);
       dft<T, R, -1>(x[f]);
     }
     C2<T> y[NFO][R];

@@ -7,13 +7,17 @@ workload (Bogacki-Shampine with rtol = atol = 1e-6 and the stop test of Section 
 state): its accepted steps (t, h) and, per step, the outside-iteration counts of k1 (that of
 the previous step's k4 when k1 was reused), k2 and k3.  (Uniform steps of T/N are unstable for
 this explicit scheme with n = 30 near the critical state, so the steps come from the adaptive
-run.)  The frozen map warm-starts every call from the previous one (the first one cold).
-Target: h_z(T) of the same frozen map with a second jc map (seed 6).
-Loss L = 1/2 dx dy sum (h_z(T) - target)^2.
+run; the same frozen steps are unstable for another jc map too.)  The frozen map warm-starts
+every call from the previous one (the first one cold).
+Target: h_z(T) of the oracle's own adaptive run (same tolerances and start) with a second jc map
+(seed 6).  Loss L = 1/2 dx dy sum (h_z(T) - target)^2.
 
 Stored (tests/golden/adjoint_<workload>.json): T, the steps, the counts, L, dL/d(knot values),
 dL/djc at 32 seeded random film cells, and the directional derivatives <dL/djc, d> for two
-seeded directions d = jc * z (z ~ N(0,1) per cell), with the oracle's wall time.
+seeded directions d = jc * z (z ~ N(0,1) per cell), with the oracle's wall time; and, so that a
+user of the stored values can rebuild the target with an FP64 adaptive run of their own and
+check it, the target run's attempt and acceptance counts and the target's norm, sum and values
+at the 32 cells and at 32 seeded free-space cells.
 
   python tests/golden/make_adjoint_golden.py [--grid 1024] [--T 0.04] [--ckpt 20]
 """
@@ -38,7 +42,7 @@ from oracle.bs23 import BS23  # noqa: E402
 from oracle.film2d import FilmProblem  # noqa: E402
 from oracle.waveform import Waveform  # noqa: E402
 
-CELL_SEED, DIR_SEEDS = 53, (54, 55)
+CELL_SEED, DIR_SEEDS, OUT_SEED = 53, (54, 55), 56
 
 
 def problem(wl, jc):
@@ -47,8 +51,9 @@ def problem(wl, jc):
                        iter_tol=wl.iter_tol, iter_max=wl.iter_max)
 
 
-def adaptive_decisions(wl, jc):
-    """The accepted steps and per-step counts (k1, k2, k3) of the oracle's adaptive run."""
+def adaptive_run(wl, jc):
+    """The oracle's adaptive run: (accepted steps, per-step counts (k1, k2, k3), attempts,
+    h_z(T))."""
     p = problem(wl, jc)
     s = BS23(p.rhs, p.wf, rtol=wl.rtol, atol=wl.atol, on_accept=p.accept, on_attempt=p.begin_attempt)
     s.start(wl.t0, np.zeros((wl.ny, wl.nx)), wl.t1)
@@ -62,7 +67,7 @@ def adaptive_decisions(wl, jc):
         steps.append((e.t, e.h))
         counts += [int(k1), int(e.iters[1]), int(e.iters[2])]
         k4_prev = e.iters[3]
-    return steps, counts, len(s.log)
+    return steps, counts, len(s.log), p.hz(wl.t1, s.y)
 
 
 def main():
@@ -76,19 +81,20 @@ def main():
     jc6 = W.jc_map_lognormal((wl.ny, wl.nx), seed=6, sigma=0.2)
     kt, kv = wl.he_knots
     w0 = time.time()
-    steps, counts, attempts = adaptive_decisions(wl, jc)
+    steps, counts, attempts, _ = adaptive_run(wl, jc)
     print(f"adaptive run: {len(steps)} accepted steps of {attempts} attempts, mean count "
           f"{np.mean(counts):.2f}, {time.time() - w0:.0f} s", flush=True)
     g0 = np.zeros((wl.ny, wl.nx))
-    a6 = FilmAdjoint(problem(wl, jc6))
-    y6 = a6.solve(g0, jc6, kt, kv, steps, counts)
-    target = a6._he(np.array(kt), np.array(kv), args.T)[0] + a6.T(a6.p.Kh, y6)
-    print(f"target: {time.time() - w0:.0f} s", flush=True)
+    steps6, _, attempts6, target = adaptive_run(wl, jc6)
+    print(f"target: {len(steps6)} accepted steps of {attempts6} attempts, {time.time() - w0:.0f} s",
+          flush=True)
     a = FilmAdjoint(problem(wl, jc))
     L, cb, vb, _ = a.gradient(g0, jc, kt, kv, steps, target, counts, ckpt_every=args.ckpt)
     wall = time.time() - w0
     film = np.argwhere(wl.mask == 1)
     cells = film[W.rng(CELL_SEED).choice(len(film), 32, replace=False)]
+    free = np.argwhere(wl.mask == 0)
+    out_cells = free[W.rng(OUT_SEED).choice(len(free), 32, replace=False)]
     dirs = [jc * W.rng(s).standard_normal(jc.shape) for s in DIR_SEEDS]
     out = {"workload": wl.name, "grid": [wl.nx, wl.ny], "T": args.T, "n_steps": len(steps),
            "steps": [[float(t), float(h)] for t, h in steps], "adaptive_attempts": attempts,
@@ -98,12 +104,19 @@ def main():
            "cell_seed": CELL_SEED, "direction_seeds": list(DIR_SEEDS),
            "directional": [float((cb * d).sum()) for d in dirs],
            "jcbar_abs_sum": float(np.abs(cb).sum()), "jcbar_l2": float(np.linalg.norm(cb)),
+           "target_jc_seed": 6, "target_accepted": len(steps6), "target_attempts": attempts6,
+           "target_l2": float(np.linalg.norm(target)), "target_sum": float(target.sum()),
+           "target_cells": [float(target[iy, ix]) for iy, ix in cells],
+           "out_cells": out_cells.tolist(),
+           "target_out_cells": [float(target[iy, ix]) for iy, ix in out_cells],
            "oracle_seconds": wall, "fft_workers": _fft.workers(),
            "made_by": "tests/golden/make_adjoint_golden.py (oracle/ only)"}
     path = os.path.join(HERE, f"adjoint_{wl.name}.json")
     with open(path, "w") as f:
         json.dump(out, f)
-    print(json.dumps({k: v for k, v in out.items() if k not in ("counts", "cells", "jcbar_cells", "steps")}))
+    print(json.dumps({k: v for k, v in out.items()
+                      if k not in ("counts", "cells", "jcbar_cells", "steps", "out_cells", "target_cells",
+                                   "target_out_cells")}))
 
 
 if __name__ == "__main__":
