@@ -363,7 +363,7 @@ def golden_ramp_leg(native, W, torch, which: str):
     sec = time.perf_counter() - w0
     info = p.mf_get_info()
     stride = meta["field_stride"]
-    errs = []
+    errs, num, den = [], 0.0, 0.0
     for tf, fref in zip(ref["t_fields"], ref["fields"]):
         k = int(np.argmin(np.abs(t_out - tf)))
         f = fields[k].cpu().numpy()
@@ -372,15 +372,18 @@ def golden_ramp_leg(native, W, torch, which: str):
         else:
             lo, hi = wl.nx // 4 - 4, 3 * wl.nx // 4 + 4
             f = f.reshape(3, wl.nz, wl.ny, wl.nx)[:, lo:hi:stride, lo:hi:stride, lo:hi:stride]
-        errs.append(float(np.linalg.norm(f - fref) / np.linalg.norm(fref)))
+        d2, n2 = float(((f - fref) ** 2).sum()), float((fref ** 2).sum())
+        errs.append((d2 / n2) ** 0.5)
+        num, den = num + d2, den + n2
     mref = ref["m"].reshape(len(t_out), -1)
     m_err = float(np.linalg.norm(m - mref) / np.linalg.norm(mref))
     return {"workload": wl.name, "transforms": "f32", "t_end": float(t_out[-1]), "seconds": sec,
             "accepted_steps": info["n_accepted"], "rejected_steps": info["n_rejected"],
             "rhs_evals": info["n_rhs"], "outside_iterations": info["n_iters"],
-            "rel_err_m": m_err, "rel_err_field": max(errs), "field": meta["field"],
-            "tolerance": 2e-4, "oracle_seconds": meta["oracle_seconds"],
-            "oracle_fft_workers": meta["fft_workers"],
+            "rel_err_m_loop": m_err, "rel_err_field_spacetime": (num / den) ** 0.5,
+            "rel_err_field_per_snapshot": errs, "field": meta["field"],
+            "tolerance": {"m_loop": 2e-4, "field_spacetime": 4e-4 if wl.dim == 2 else 2e-4},
+            "oracle_seconds": meta["oracle_seconds"], "oracle_fft_workers": meta["fft_workers"],
             "oracle_steps": meta["attempts"]}
 
 
@@ -533,193 +536,6 @@ def run_reference(args):
             "data": "synthetic", "config": bench_config(wl),
             "run": {"step": "one right-hand side", "mean_outside_iterations": mean_it,
                     "t_reached": t_reached},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
-def golden_ramp_leg(native, W, torch, which: str):
-    """Full ramp of a stated workload on the GPU (FP32 transforms, FP64 state), free running from
-    a zero state, timed end to end (mf_run_ramp with its readouts), with its relative L2 errors
-    against the FP64 oracle's stored ramp (tests/golden/, written by make_ramp_goldens.py)."""
-    import numpy as np
-    wl = W.rect_film_2048(precision=1) if which == "film" else W.cube_bulk(128, precision=1)
-    path = os.path.join(ROOT, "tests", "golden", f"ramp_{wl.name}.npz")
-    if not os.path.exists(path):
-        return {"workload": wl.name, "skipped": "no stored oracle ramp"}
-    ref = np.load(path)
-    meta = json.load(open(path.replace(".npz", ".json")))
-    p = native.from_workload(wl)
-    t_out = ref["t_out"]
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    m, fields = p.mf_run_ramp(t_out, want_fields=True)
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - w0
-    info = p.mf_get_info()
-    stride = meta["field_stride"]
-    errs = []
-    for tf, fref in zip(ref["t_fields"], ref["fields"]):
-        k = int(np.argmin(np.abs(t_out - tf)))
-        f = fields[k].cpu().numpy()
-        if wl.dim == 2:
-            f = f.reshape(wl.ny, wl.nx)[::stride, ::stride]
-        else:
-            lo, hi = wl.nx // 4 - 4, 3 * wl.nx // 4 + 4
-            f = f.reshape(3, wl.nz, wl.ny, wl.nx)[:, lo:hi:stride, lo:hi:stride, lo:hi:stride]
-        errs.append(float(np.linalg.norm(f - fref) / np.linalg.norm(fref)))
-    mref = ref["m"].reshape(len(t_out), -1)
-    m_err = float(np.linalg.norm(m - mref) / np.linalg.norm(mref))
-    return {"workload": wl.name, "transforms": "f32", "t_end": float(t_out[-1]), "seconds": sec,
-            "accepted_steps": info["n_accepted"], "rejected_steps": info["n_rejected"],
-            "rhs_evals": info["n_rhs"], "outside_iterations": info["n_iters"],
-            "rel_err_m": m_err, "rel_err_field": max(errs), "field": meta["field"],
-            "tolerance": 2e-4, "oracle_seconds": meta["oracle_seconds"],
-            "oracle_fft_workers": meta["fft_workers"],
-            "oracle_steps": meta["attempts"]}
-
-
-def fp64_leg(native, W, torch, steps: int = 5, warmup: int = 3):
-    """Secondary line: the same film and start with FP64 transforms (the plain FP64 solver),
-    timed like the main line, and the precision form's speed-up over it."""
-    wl = W.rect_film_2048(precision=0)
-    p = native.from_workload(wl)
-    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
-    p.mf_set_state(T_START, torch.as_tensor(g0, device="cuda"), h=H_START)
-    p.mf_advance(1.0, max_attempts=warmup)
-    torch.cuda.synchronize()
-    i0 = p.mf_get_info()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(p.stream)
-    p.mf_advance(1.0, max_attempts=steps)
-    e1.record(p.stream)
-    torch.cuda.synchronize()
-    i1 = p.mf_get_info()
-    sec = e0.elapsed_time(e1) / 1000.0
-    n_rhs, n_it = i1["n_rhs"] - i0["n_rhs"], i1["n_iters"] - i0["n_iters"]
-    M = wl.nx * wl.ny * 8.0
-    alg = rhs_bytes(n_rhs, n_it, M)
-    peak, kind = hbm_peak()
-    return {"workload": wl.name, "transforms": "f64", "value": n_rhs / sec, "unit": UNIT,
-            "steps": i1["n_attempts"] - i0["n_attempts"], "rhs_evals": n_rhs,
-            "mean_outside_iterations": n_it / max(n_rhs, 1),
-            "ms_per_round_trip": 1000.0 * sec / (2 * n_rhs + 2 * n_it),
-            "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
-                         "bytes_model": "(19 + 14 I) M per RHS, M = 2048^2 x 8 B"}}
-
-
-def cufft_leg(torch, n: int = 2048, reps: int = 50):
-    """Reference point only (the library never calls it): cuFFT round trips
-    irfft2(M * rfft2(x)) of an n x n real field through torch.fft, in FP32 and FP64, CUDA-event
-    timed after warm-up."""
-    out = {"grid": [n, n], "note": "torch.fft (cuFFT) round trip with a pointwise multiplier; "
-                                   "timed beside the library as a reference point only"}
-    for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
-        x = torch.randn(n, n, device="cuda", dtype=dt)
-        mult = torch.rand(n, n // 2 + 1, device="cuda", dtype=dt)
-
-        def rt():
-            return torch.fft.irfft2(torch.fft.rfft2(x) * mult, s=(n, n))
-        for _ in range(5):
-            rt()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            rt()
-        e1.record()
-        torch.cuda.synchronize()
-        out[f"ms_per_round_trip_{name}"] = e0.elapsed_time(e1) / reps
-    return out
-
-
-def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
-    """Whole-job figures of a multi-rank run: the slowest rank's timed seconds, the evaluations of
-    all ranks and the sum of the ranks' end-to-end rates (the replicas run side by side).
-    `dist` is torch.distributed with an initialised process group, or None for one rank."""
-    if dist is None:
-        return sec, float(n_rhs), e2e_rate
-    import torch
-    mx = torch.tensor([sec], device=device, dtype=torch.float64)
-    sm = torch.tensor([float(n_rhs), e2e_rate], device=device, dtype=torch.float64)
-    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-    return float(mx[0]), float(sm[0]), float(sm[1])
-
-
-def cores_used() -> int:
-    """Host threads of the oracle's transforms (scipy.fft workers); its elementwise steps run on
-    one thread."""
-    from oracle import _fft
-    return _fft.workers()
-
-
-T_START = 0.05          # the timed steps start mid-cycle from a seeded critical-state film
-H_START = 2e-5
-
-
-def bench_config(wl) -> dict:
-    """The workload both arms time (identical in the two JSON lines)."""
-    return {"workload": wl.name, "grid": [wl.nx, wl.ny], "film_cells": [wl.nx // 2, wl.ny // 4],
-            "n": wl.n, "he": "0.8 sin(2 pi t)", "rtol": wl.rtol, "atol": wl.atol,
-            "iter_tol": wl.iter_tol, "outside_iteration": "converged, warm-started (Section 2.2)",
-            "start": f"seeded critical-state film at t = {T_START}, h = {H_START}, after the warm-up",
-            "l2": "working set > L2 (no flush)"}
-
-
-class _Enough(Exception):
-    pass
-
-
-def run_reference(args):
-    """The oracle (FP64, CPU) on the same workload and start state as the GPU arm: its own
-    Bogacki-Shampine integrator and warm-started outside iteration, W right-hand sides of
-    warm-up, then exactly K timed right-hand sides (one step of this arm = one right-hand side,
-    the unit of the metric)."""
-    import numpy as np
-    import workloads as W
-    from oracle.bs23 import BS23
-    wl = W.rect_film_2048(precision=0)
-    o = _oracle_problem(wl)
-    g0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=100, amplitude=0.3)
-    W_, K = max(1, args.warmup), max(1, args.steps)
-    marks = {}
-    iters = []
-
-    def rhs(t, y, seg, force):
-        n = len(iters)
-        if n == W_:
-            marks["t0"] = time.perf_counter()
-        r = o.rhs(t, y, seg, force)
-        iters.append(r[1])
-        if len(iters) == W_ + K:
-            marks["t1"] = time.perf_counter()
-            raise _Enough
-        return r
-
-    s = BS23(rhs, o.wf, rtol=wl.rtol, atol=wl.atol, h0=H_START, on_accept=o.accept,
-             on_attempt=o.begin_attempt)
-    s.start(T_START, g0, 1.0)
-    try:
-        s.advance(1.0)
-    except _Enough:
-        pass
-    el = marks["t1"] - marks["t0"]
-    rate = K / el
-    timed_iters = iters[W_:]
-    cores = cores_used()
-    sample = (f"{K} right-hand sides (after {W_} of warm-up) of the oracle's own BS23 run of the "
-              f"{wl.nx}x{wl.ny} film from the GPU arm's start state: converged warm-started outside "
-              f"iterations, mean {np.mean(timed_iters):.1f}; transforms on {cores} threads, "
-              f"elementwise steps on one")
-    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": K, "warmup": W_, "ms_per_step": 1000.0 * el / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": bench_config(wl),
-            "run": {"step": "one right-hand side", "mean_outside_iterations": float(np.mean(timed_iters)),
-                    "t_reached": s.t},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
