@@ -38,6 +38,7 @@ struct Bulk {
   const Desc& d;
   C2<T>* sm;
   C2<T>* sm2;
+  C2<T>* sm3;        // third buffer: the next item's gather in the y and z passes
   Shared& sh;
   int nx, ny, nz, lgx, lgy, lgz, half, nkx;
   long long nspec, ncell;
@@ -52,7 +53,7 @@ struct Bulk {
   unsigned nblocks;
 
   __device__ Bulk(const Desc& dd, C2<T>* s, Shared& shr)
-      : d(dd), sm(s), sm2(s + BATCH_PAD), sh(shr) {
+      : d(dd), sm(s), sm2(s + BATCH_PAD), sm3(s + 2 * BATCH_PAD), sh(shr) {
     nx = d.nx; ny = d.ny; nz = d.nz; lgx = d.lgx; lgy = d.lgy; lgz = d.lgz;
     half = nx / 2; nkx = half + 1;
     nspec = (long long)nkx * ny * nz;
@@ -136,142 +137,159 @@ struct Bulk {
     return reduce_partials(d.partials, d.max_items, slot, (ny / rb) * nz, is_max, sh.red);
   }
 
+  // ---- the y and z passes: items it = blockIdx.x, + gridDim.x, ... with the gather of the next
+  // item in flight (cp.async into the third shared buffer) while the current one transforms in
+  // the other two.  issue(it, buf) starts item it's gather into buf; work(it, a, b) transforms
+  // the item gathered in a (b is its second buffer), writes its result and ends with a CTA
+  // barrier.  The buffers rotate: the next input is the prefetch buffer, the next prefetch goes
+  // to the buffer the finished item used last. ----
+  template <class Issue, class Work>
+  __device__ __forceinline__ void pipelined(int nitems, Issue issue, Work work) {
+    C2<T>* a = sm;
+    C2<T>* b = sm2;
+    C2<T>* c = sm3;
+    int it = (int)blockIdx.x;
+    if (it < nitems) issue(it, a);
+    for (; it < nitems; it += (int)gridDim.x) {
+      const int nxt = it + (int)gridDim.x;
+      if (nxt < nitems) {
+        issue(nxt, c);
+        cp_async_wait<1>();                 // this item's group; the next one stays in flight
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      work(it, a, b);
+      C2<T>* const t = a;
+      a = c;
+      c = b;
+      b = t;
+    }
+  }
+
   // ---- y pass, forward: S1[c][z][kx][:] -> S2[c][kx][:][z] for z in [z0, z0 + zs) ----
   __device__ __noinline__ void yfwd() {
-    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
-    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
-    const long long nspec = this->nspec, ncell = this->ncell;
-    C2<T>* const sm = this->sm;
-    C2<T>* const sm2 = this->sm2;
+    const int ny = this->ny, nz = this->nz, lgy = this->lgy, nkx = this->nkx, zs = this->zs;
+    const long long nspec = this->nspec;
     C2<T>* const S1 = this->S1;
     C2<T>* const S2 = this->S2;
     const C2<T>* const twy = this->twy;
-    const C2<T>* const twz = this->twz;
-    const T* const ktab = this->ktab;
-    const T* const gtab = this->gtab;
-    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
-    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
-    const int nitems = nkx * per_kx;
-    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
-      const int kx = it / per_kx, z0 = (it % per_kx) * zs;
-      const int nl = 3 * zs;
-      gather_batched<T, 4>(sm, S1, nl << lgy,
-          [=](int e) {
-            const int l = e >> lgy, y = e & (ny - 1);
-            const int c = l / zs, dz = l - c * zs;
-            return c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y;
-          },
-          [](int e) { return e; });
-      const C2<T>* X = fft_lines<T, -1>(sm, sm2, lgy, nl, twy);
-      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
-        const int dz = e % zs, rest = e / zs;
-        const int ky = rest & (ny - 1), c = rest >> lgy;
-        S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz] = X[sp(((c * zs + dz) << lgy) + ky)];
-      }
-      __syncthreads();
-    }
+    const int nl = 3 * zs;
+    pipelined(nkx * per_kx,
+        [=](int it, C2<T>* buf) {
+          const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+          gather_async<T>(buf, S1, nl << lgy,
+              [=](int e) {
+                const int l = e >> lgy, y = e & (ny - 1);
+                const int c = l / zs, dz = l - c * zs;
+                return c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y;
+              },
+              [](int e) { return e; });
+        },
+        [=](int it, C2<T>* a, C2<T>* b) {
+          const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+          const C2<T>* X = fft_lines<T, -1>(a, b, lgy, nl, twy);
+          for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+            const int dz = e % zs, rest = e / zs;
+            const int ky = rest & (ny - 1), c = rest >> lgy;
+            S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz] = X[sp(((c * zs + dz) << lgy) + ky)];
+          }
+          __syncthreads();
+        });
   }
   // ---- y pass, inverse: S2 -> S1 ----
   __device__ __noinline__ void yinv() {
-    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
-    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
-    const long long nspec = this->nspec, ncell = this->ncell;
-    C2<T>* const sm = this->sm;
-    C2<T>* const sm2 = this->sm2;
+    const int ny = this->ny, nz = this->nz, lgy = this->lgy, nkx = this->nkx, zs = this->zs;
+    const long long nspec = this->nspec;
     C2<T>* const S1 = this->S1;
     C2<T>* const S2 = this->S2;
     const C2<T>* const twy = this->twy;
-    const C2<T>* const twz = this->twz;
-    const T* const ktab = this->ktab;
-    const T* const gtab = this->gtab;
-    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
-    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = nz / zs;
-    const int nitems = nkx * per_kx;
-    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
-      const int kx = it / per_kx, z0 = (it % per_kx) * zs;
-      const int nl = 3 * zs;
-      gather_batched<T, 4>(sm, S2, nl << lgy,
-          [=](int e) {
-            const int dz = e % zs, rest = e / zs;
-            const int ky = rest & (ny - 1), c = rest >> lgy;
-            return c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz;
-          },
-          [=](int e) {
-            const int dz = e % zs, rest = e / zs;
-            const int ky = rest & (ny - 1), c = rest >> lgy;
-            return ((c * zs + dz) << lgy) + ky;
-          });
-      const C2<T>* X = fft_lines<T, +1>(sm, sm2, lgy, nl, twy);
-      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
-        const int l = e >> lgy, y = e & (ny - 1);
-        const int c = l / zs, dz = l - c * zs;
-        S1[c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y] = X[sp(e)];
-      }
-      __syncthreads();
-    }
+    const int nl = 3 * zs;
+    pipelined(nkx * per_kx,
+        [=](int it, C2<T>* buf) {
+          const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+          gather_async<T>(buf, S2, nl << lgy,
+              [=](int e) {
+                const int dz = e % zs, rest = e / zs;
+                const int ky = rest & (ny - 1), c = rest >> lgy;
+                return c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz;
+              },
+              [=](int e) {
+                const int dz = e % zs, rest = e / zs;
+                const int ky = rest & (ny - 1), c = rest >> lgy;
+                return ((c * zs + dz) << lgy) + ky;
+              });
+        },
+        [=](int it, C2<T>* a, C2<T>* b) {
+          const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+          const C2<T>* X = fft_lines<T, +1>(a, b, lgy, nl, twy);
+          for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+            const int l = e >> lgy, y = e & (ny - 1);
+            const int c = l / zs, dz = l - c * zs;
+            S1[c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny + y] = X[sp(e)];
+          }
+          __syncthreads();
+        });
   }
   // ---- z pass: forward, 3x3 multiplier, inverse on lines (kx, ky0 .. ky0 + P) ----
   __device__ __noinline__ void zpass(int op) {
-    const int nx = this->nx, ny = this->ny, nz = this->nz, lgy = this->lgy, lgz = this->lgz;
-    const int nkx = this->nkx, half = this->half, zs = this->zs, P = this->P;
+    const int ny = this->ny, nz = this->nz, lgz = this->lgz, nkx = this->nkx, half = this->half, P = this->P;
     const long long nspec = this->nspec, ncell = this->ncell;
-    C2<T>* const sm = this->sm;
-    C2<T>* const sm2 = this->sm2;
-    C2<T>* const S1 = this->S1;
     C2<T>* const S2 = this->S2;
-    const C2<T>* const twy = this->twy;
     const C2<T>* const twz = this->twz;
     const T* const ktab = this->ktab;
     const T* const gtab = this->gtab;
-    (void)nx; (void)nz; (void)lgz; (void)half; (void)zs; (void)P; (void)ncell; (void)S1; (void)S2;
-    (void)twy; (void)twz; (void)ktab; (void)gtab; (void)lgy; (void)nkx; (void)ny; (void)nspec;
     const int per_kx = ny / P;
-    const int nitems = nkx * per_kx;
     const T s = (T)1 / (T)ncell;
-    for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
-      const int kx = it / per_kx, ky0 = (it % per_kx) * P;
-      const long long base = ((long long)kx * ny + ky0) * nz;
-      const int pl = P << lgz;                       // values per component
-      gather_batched<T, 4>(sm, S2, 3 * pl,
-          [=](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
-          [](int e) { return e; });
-      C2<T>* X = fft_lines<T, -1>(sm, sm2, lgz, 3 * P, twz);
-      C2<T>* Y = X == sm ? sm2 : sm;
-      const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
-      const T kxo = kx == half ? (T)0 : kxv;
-      for (int e = threadIdx.x; e < pl; e += NT) {
-        const int p = e >> lgz, kz = e & (nz - 1);
-        const int ky = ky0 + p;
-        const T kyv = ldg_tab(&ktab[nkx + ky]), kzv = ldg_tab(&ktab[nkx + ny + kz]);
-        const T kyo = ky == ny / 2 ? (T)0 : kyv;
-        const T kzo = kz == nz / 2 ? (T)0 : kzv;
-        const C2<T> a = X[sp(e)], b = X[sp(pl + e)], c = X[sp(2 * pl + e)];
-        // cross product k x v with the odd (Nyquist-free) wavenumbers
-        C2<T> cx = {kyo * c.x - kzo * b.x, kyo * c.y - kzo * b.y};
-        C2<T> cy = {kzo * a.x - kxo * c.x, kzo * a.y - kxo * c.y};
-        C2<T> cz = {kxo * b.x - kyo * a.x, kxo * b.y - kyo * a.y};
-        T f;
-        if (op == OP3_PHI) {
-          const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-          f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
-        } else {
-          const T G = gx * ldg_tab(&gtab[nkx + ky]) * ldg_tab(&gtab[nkx + ny + kz]);
-          f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
-        }
-        X[sp(e)] = cmul_si(cscale(cx, f), 1);
-        X[sp(pl + e)] = cmul_si(cscale(cy, f), 1);
-        X[sp(2 * pl + e)] = cmul_si(cscale(cz, f), 1);
-      }
-      __syncthreads();
-      const C2<T>* Z = fft_lines<T, +1>(X, Y, lgz, 3 * P, twz);
-      for (int e = threadIdx.x; e < 3 * pl; e += NT) {
-        const int c = e / pl, r = e - c * pl;
-        S2[c * nspec + base + r] = Z[sp(e)];
-      }
-      __syncthreads();
-    }
+    const int pl = P << lgz;                         // values per component
+    pipelined(nkx * per_kx,
+        [=](int it, C2<T>* buf) {
+          const int kx = it / per_kx, ky0 = (it % per_kx) * P;
+          const long long base = ((long long)kx * ny + ky0) * nz;
+          gather_async<T>(buf, S2, 3 * pl,
+              [=](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
+              [](int e) { return e; });
+        },
+        [=](int it, C2<T>* a, C2<T>* b) {
+          const int kx = it / per_kx, ky0 = (it % per_kx) * P;
+          const long long base = ((long long)kx * ny + ky0) * nz;
+          C2<T>* X = fft_lines<T, -1>(a, b, lgz, 3 * P, twz);
+          C2<T>* Y = X == a ? b : a;
+          const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
+          const T kxo = kx == half ? (T)0 : kxv;
+          for (int e = threadIdx.x; e < pl; e += NT) {
+            const int p = e >> lgz, kz = e & (nz - 1);
+            const int ky = ky0 + p;
+            const T kyv = ldg_tab(&ktab[nkx + ky]), kzv = ldg_tab(&ktab[nkx + ny + kz]);
+            const T kyo = ky == ny / 2 ? (T)0 : kyv;
+            const T kzo = kz == nz / 2 ? (T)0 : kzv;
+            const C2<T> va = X[sp(e)], vb = X[sp(pl + e)], vc = X[sp(2 * pl + e)];
+            // cross product k x v with the odd (Nyquist-free) wavenumbers
+            C2<T> cx = {kyo * vc.x - kzo * vb.x, kyo * vc.y - kzo * vb.y};
+            C2<T> cy = {kzo * va.x - kxo * vc.x, kzo * va.y - kxo * vc.y};
+            C2<T> cz = {kxo * vb.x - kyo * va.x, kxo * vb.y - kyo * va.y};
+            T f;
+            if (op == OP3_PHI) {
+              const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+              f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
+            } else {
+              const T G = gx * ldg_tab(&gtab[nkx + ky]) * ldg_tab(&gtab[nkx + ny + kz]);
+              f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
+            }
+            X[sp(e)] = cmul_si(cscale(cx, f), 1);
+            X[sp(pl + e)] = cmul_si(cscale(cy, f), 1);
+            X[sp(2 * pl + e)] = cmul_si(cscale(cz, f), 1);
+          }
+          __syncthreads();
+          const C2<T>* Z = fft_lines<T, +1>(X, Y, lgz, 3 * P, twz);
+          for (int e = threadIdx.x; e < 3 * pl; e += NT) {
+            const int c = e / pl, r = e - c * pl;
+            S2[c * nspec + base + r] = Z[sp(e)];
+          }
+          __syncthreads();
+        });
   }
 
   // Yf, Z(op), Yi with barriers; the x passes before and after are separate

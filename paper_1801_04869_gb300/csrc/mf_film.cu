@@ -10,7 +10,10 @@ __global__ void __launch_bounds__(NT, 2) film_kernel(const Desc* __restrict__ dg
   film_main<T>(*dg, a, (int)blockIdx.x, gridDim.x);
 }
 
-size_t kernel_smem_bytes(const Desc& d) { return film_smem_bytes(d.precision); }
+// film passes: two FFT buffers; bulk passes: a third one for the next item's gather
+size_t kernel_smem_bytes(const Desc& d) {
+  return film_smem_bytes(d.precision) / 2 * (d.dim == 3 ? 3 : 2);
+}
 
 int film_max_blocks(int precision, size_t smem) {
   int nb = 0;

@@ -117,6 +117,27 @@ __device__ __forceinline__ void lines_store(const C2<T>* sm, C2<T>* dst, long lo
   __syncthreads();
 }
 
+// Asynchronous copies global -> shared (cp.async): issued without a register round trip,
+// complete at cp_async_wait (this thread's groups; a CTA barrier after it makes every thread's
+// copies visible).  gather_async issues value e from src[goff(e)] to sm[sp(soff(e))] for
+// e < total as one group.
+__device__ __forceinline__ void cp_async_c2(C2<float>* s, const C2<float>* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_c2(C2<double>* s, const C2<double>* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+template <typename T, class GOff, class SOff>
+__device__ __forceinline__ void gather_async(C2<T>* sm, const C2<T>* src, int total, GOff goff, SOff soff) {
+  for (int e = threadIdx.x; e < total; e += NT) cp_async_c2(sm + sp(soff(e)), src + goff(e));
+  cp_async_commit();
+}
+
 // Gather `total` complex values into shared memory, value e from src[goff(e)] to
 // sm[sp(soff(e))], with U loads in flight per thread; synchronises at the end.
 template <typename T, int U, class GOff, class SOff>
