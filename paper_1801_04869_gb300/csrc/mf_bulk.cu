@@ -82,8 +82,16 @@ struct Bulk {
   }
 
   // ---- x pass over rows (z, y0 .. y0 + rb): inverse of NIN = 0|3 fields, epilogue, forward ----
+  // With inputs, the item's half spectra arrive staged in the third buffer (cp.async); once the
+  // first inverse stage has read them, the next item's (x pass item `next`, -1: none) are
+  // issued into the same buffer and load while this item finishes.
+  __device__ __forceinline__ void xstage(int it, int nin) {
+    const int per_z = ny / rb;
+    const long long off = (long long)(it / per_z) * nkx * ny + (it % per_z) * rb;
+    if (nin == 3) stage_rows_async<T, 3>(sm3, S1 + off, nspec, ny, rb, lgx);
+  }
   template <int NIN, int NOUT, class Epi>
-  __device__ __forceinline__ void xitem(int z, int y0, Epi& epi_io) {
+  __device__ __forceinline__ void xitem(int z, int y0, int next, Epi& epi_io) {
     Epi epi = epi_io;                   // register copy of the epilogue
     const int nx = this->nx, ny = this->ny, lgx = this->lgx, nkx = this->nkx, rb = this->rb;
     const long long nspec = this->nspec;
@@ -95,7 +103,14 @@ struct Bulk {
     const long long off = (long long)z * nkx * ny + y0;
     C2<T>* X = sm;
     const int lgpair = __ffs(npair) - 1;
-    if constexpr (NIN > 0) X = rows_gather_inverse<T, NIN>(sm, sm2, S1 + off, nspec, ny, npair, lgpair, lgx, twx);
+    (void)off;
+    if constexpr (NIN > 0) {
+      cp_async_wait<0>();
+      __syncthreads();
+      X = rows_inverse_staged<T, NIN>(sm3, sm, sm2, npair, lgpair, lgx, twx, [&] {
+        if (next >= 0) xstage(next, NIN);
+      });
+    }
     C2<T>* Y = X == sm ? sm2 : sm;
     // not unrolled: a second cell in flight spilled the epilogues' live values (26% slower
     // per outside iteration on the 128^3 grid)
@@ -109,8 +124,12 @@ struct Bulk {
         ina[f] = v.x; inb[f] = v.y;
       }
       const long long i0 = ((long long)z * ny + y0 + 2 * pr) * nx + x;
-      epi(i0, ina, oa);
-      epi(i0 + nx, inb, ob);
+      if constexpr (Epi::kPair) {
+        epi.pair(i0, i0 + nx, ina, inb, oa, ob);
+      } else {
+        epi(i0, ina, oa);
+        epi(i0 + nx, inb, ob);
+      }
 #pragma unroll
       for (int f = 0; f < NOUT; ++f) X[sp(((f * npair + pr) << lgx) + x)] = C2<T>{oa[f], ob[f]};
     }
@@ -123,10 +142,12 @@ struct Bulk {
   __device__ void xpass(Epi& epi, int slot) {
     const int per_z = ny / rb;
     const int nitems = per_z * nz;
+    if (NIN > 0 && (int)blockIdx.x < nitems) xstage((int)blockIdx.x, NIN);
     for (int it = (int)blockIdx.x; it < nitems; it += (int)gridDim.x) {
       epi.acc = 0.0;
       epi.accmax = 0.0;
-      xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, epi);
+      const int next = it + (int)gridDim.x < nitems ? it + (int)gridDim.x : -1;
+      xitem<NIN, NOUT>(it / per_z, (it % per_z) * rb, next, epi);
       if (slot >= 0) {
         const double v = epi.is_max ? block_max(epi.accmax, sh.red) : block_sum(epi.acc, sh.red);
         if (threadIdx.x == 0) d.partials[(size_t)slot * d.max_items + it] = v;
@@ -316,15 +337,21 @@ struct BStage : EpiBase<T> {
   StageIn in;
   bool kim;
   __device__ void operator()(long long i, const T*, T* out) {
+    // every load of the cell before its first store (a store could alias a later load as far
+    // as the compiler knows, which would put each load behind the previous store)
+    double v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = in.y[c * P.ncell + i];
+    for (int j = 0; j < in.nk; ++j) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] += in.c[j] * in.k[j][c * P.ncell + i];
+    }
     double h2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long k = c * P.ncell + i;
-      double v = in.y[k];
-      for (int j = 0; j < in.nk; ++j) v += in.c[j] * in.k[j][k];
-      if (in.ynew) in.ynew[k] = v;
-      out[c] = (T)v;
-      h2 += v * v;
+      if (in.ynew) in.ynew[c * P.ncell + i] = v[c];
+      out[c] = (T)v[c];
+      h2 += v[c] * v[c];
     }
     if (kim && __ldg(&P.mask[i]) == 1) P.hd[i] = (T)sqrt(h2);
   }
@@ -357,15 +384,24 @@ struct BInit : EpiBase<T> {                // h_dot^0: h_dot_in on the conductor
   BulkPtrs<T> P;
   bool warm;
   T hed[3];
-  __device__ void operator()(long long i, const T* in, T* out) {
-    const bool cond = __ldg(&P.mask[i]) != 0;
+  static constexpr bool kPair = true;
+  __device__ __forceinline__ void pair(long long ia, long long ib, const T* ina, const T* inb, T* oa, T* ob) {
+    const bool ca = __ldg(&P.mask[ia]) != 0, cb = __ldg(&P.mask[ib]) != 0;
+    T wa[3], wb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      T h;
-      if (cond) h = in[c];                                 // -curl e (Eq. 14)
-      else h = warm ? P.hd[c * P.ncell + i] : hed[c];
-      P.hd[c * P.ncell + i] = h;
-      out[c] = h;
+      wa[c] = (!ca && warm) ? P.hd[c * P.ncell + ia] : hed[c];
+      wb[c] = (!cb && warm) ? P.hd[c * P.ncell + ib] : hed[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      oa[c] = ca ? ina[c] : wa[c];                         // -curl e (Eq. 14) on the conductor
+      ob[c] = cb ? inb[c] : wb[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      P.hd[c * P.ncell + ia] = oa[c];
+      P.hd[c * P.ncell + ib] = ob[c];
     }
   }
 };
@@ -383,22 +419,30 @@ template <typename T>
 struct BUpdate : EpiBase<T, T> {           // Eq. 18 on free space, residual, forward
   BulkPtrs<T> P;
   T hed[3];
-  __device__ void operator()(long long i, const T* in, T* out) {
-    if (__ldg(&P.mask[i]) == 0) {
-      T s2 = 0;
+  static constexpr bool kPair = true;
+  __device__ __forceinline__ void pair(long long ia, long long ib, const T* ina, const T* inb, T* oa, T* ob) {
+    const bool fa = __ldg(&P.mask[ia]) == 0, fb = __ldg(&P.mask[ib]) == 0;
+    T ha[3], hb[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T hn = hed[c] + in[c];
-        const T ho = P.hd[c * P.ncell + i];
-        const T df = hn - ho;
-        s2 += df * df;
-        P.hd[c * P.ncell + i] = hn;
-        out[c] = hn;
-      }
-      this->acc += sqrt(s2);
-    } else {
+    for (int c = 0; c < 3; ++c) {
+      ha[c] = P.hd[c * P.ncell + ia];
+      hb[c] = P.hd[c * P.ncell + ib];
+    }
+    T sa = 0, sb = 0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[c] = P.hd[c * P.ncell + i];
+    for (int c = 0; c < 3; ++c) {
+      const T na = hed[c] + ina[c], nb = hed[c] + inb[c];
+      sa += (na - ha[c]) * (na - ha[c]);
+      sb += (nb - hb[c]) * (nb - hb[c]);
+      oa[c] = fa ? na : ha[c];
+      ob[c] = fb ? nb : hb[c];
+    }
+    if (fa) this->acc += sqrt(sa);
+    if (fb) this->acc += sqrt(sb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (fa) P.hd[c * P.ncell + ia] = oa[c];
+      if (fb) P.hd[c * P.ncell + ib] = ob[c];
     }
   }
 };
@@ -411,20 +455,23 @@ struct BFinal : EpiBase<T> {               // h_dot out (FP64); optional BS23 er
   double h, rtol, atol;
   const double* k1; const double* k2; const double* k3; const double* y; const double* ynew;
   __device__ void operator()(long long i, const T*, T*) {
+    double g[3];                                             // loads before the stores (see BStage)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] = (double)P.hd[c * P.ncell + i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) kout[c * P.ncell + i] = g[c];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long k = c * P.ncell + i;
-      const double g = (double)P.hd[k];
-      kout[k] = g;
       if (err) {
-        const double E = h * (-5.0 / 72.0 * k1[k] + 1.0 / 12.0 * k2[k] + 1.0 / 9.0 * k3[k] - 0.125 * g);
+        const double E = h * (-5.0 / 72.0 * k1[k] + 1.0 / 12.0 * k2[k] + 1.0 / 9.0 * k3[k] - 0.125 * g[c]);
         const double sc = atol + rtol * fmax(fabs(y[k]), fabs(ynew[k]));
         double q;                                            // the ratio in the transform precision
         if constexpr (sizeof(T) == 4) q = (double)__fdiv_rn((float)fabs(E), (float)sc);
         else q = fabs(E) / sc;
         if (!(q == q) || isinf(q)) q = 1e300;
         this->accmax = fmax(this->accmax, q);
-      } else if (!isfinite(g)) {
+      } else if (!isfinite(g[c])) {
         this->accmax = 1.0;
       }
     }

@@ -306,8 +306,12 @@ struct Film {
         }
       }
       const long long i0 = (long long)(y0 + 2 * pr) * nx + x0;
-      epi(i0, ina, oa);
-      epi(i0 + nx, inb, ob);
+      if constexpr (Epi::kPair) {
+        epi.pair(i0, i0 + nx, ina, inb, oa, ob);
+      } else {
+        epi(i0, ina, oa);
+        epi(i0 + nx, inb, ob);
+      }
 #pragma unroll
       for (int f = 0; f < NOUT; ++f) {
 #pragma unroll
@@ -465,21 +469,38 @@ struct EpiInit : EpiBase<T, T> {
   bool warm;
   const T* wsrc;          // warm start (the previous time step's or the most recent iterate)
   T A_prev, hed;
-  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(P.mask + i);
-    V4<T> w;
-    if (warm) w = ld4(wsrc + i);
-    const V4<T> q1 = ldg4(P.q1 + i);
+  struct Ld { uchar4 m; V4<T> w, q1; };
+  __device__ __forceinline__ Ld load(long long i) const {
+    Ld l;
+    l.m = ldmask4(P.mask + i);
+    if (warm) l.w = ld4(wsrc + i);
+    l.q1 = ldg4(P.q1 + i);
+    return l;
+  }
+  __device__ __forceinline__ V4<T> apply(const Ld& l, const V4<T>* in) {
     V4<T> h;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (mask_at(m, q) != 0) h.v[q] = in[0].v[q];             // h_dot_in on the conductor
-      else h.v[q] = warm ? w.v[q] - A_prev : hed;             // warm start (Section 2.2)
+      if (mask_at(l.m, q) != 0) h.v[q] = in[0].v[q];           // h_dot_in on the conductor
+      else h.v[q] = warm ? l.w.v[q] - A_prev : hed;           // warm start (Section 2.2)
       this->acc += h.v[q];
-      this->acc2 += q1.v[q] * h.v[q];                         // <q1, h> for C
+      this->acc2 += l.q1.v[q] * h.v[q];                       // <q1, h> for C
     }
+    return h;
+  }
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const V4<T> h = apply(load(i), in);
     st4(P.hd + i, h);
     out[0] = h;
+  }
+  static constexpr bool kPair = true;
+  __device__ __forceinline__ void pair(long long ia, long long ib, const V4<T>* ina, const V4<T>* inb,
+                                       V4<T>* oa, V4<T>* ob) {
+    const Ld la = load(ia), lb = load(ib);
+    oa[0] = apply(la, ina);
+    ob[0] = apply(lb, inb);
+    st4(P.hd + ia, oa[0]);
+    st4(P.hd + ib, ob[0]);
   }
 };
 
@@ -510,18 +531,32 @@ template <typename T>
 struct EpiUpdate : EpiBase<T, T> {
   FilmPtrs<T> P;
   T A;
-  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
-    const uchar4 m = ldmask4(P.mask + i);
-    V4<T> h = ld4(P.hd + i);
-    const V4<T> q1 = ldg4(P.q1 + i);
+  struct Ld { uchar4 m; V4<T> h, q1; };
+  __device__ __forceinline__ Ld load(long long i) const {
+    return Ld{ldmask4(P.mask + i), ld4(P.hd + i), ldg4(P.q1 + i)};
+  }
+  __device__ __forceinline__ V4<T> apply(Ld l, const V4<T>* in) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (mask_at(m, q) == 0) h.v[q] = (h.v[q] - A) - in[0].v[q];
-      this->acc += h.v[q];
-      this->acc2 += q1.v[q] * h.v[q];
+      if (mask_at(l.m, q) == 0) l.h.v[q] = (l.h.v[q] - A) - in[0].v[q];
+      this->acc += l.h.v[q];
+      this->acc2 += l.q1.v[q] * l.h.v[q];
     }
+    return l.h;
+  }
+  __device__ void operator()(long long i, const V4<T>* in, V4<T>* out) {
+    const V4<T> h = apply(load(i), in);
     st4(P.hd + i, h);
     out[0] = h;
+  }
+  static constexpr bool kPair = true;
+  __device__ __forceinline__ void pair(long long ia, long long ib, const V4<T>* ina, const V4<T>* inb,
+                                       V4<T>* oa, V4<T>* ob) {
+    const Ld la = load(ia), lb = load(ib);
+    oa[0] = apply(la, ina);
+    ob[0] = apply(lb, inb);
+    st4(P.hd + ia, oa[0]);
+    st4(P.hd + ib, ob[0]);
   }
 };
 
@@ -540,9 +575,11 @@ struct EpiFinal : EpiBase<T> {
     V4<double> g;
 #pragma unroll
     for (int q = 0; q < 4; ++q) g.v[q] = mask_at(m, q) != 0 ? (double)u.v[q] : 0.0;
-    st4(kout + i, g);
     if (err) {
+      // the loads before the store (a store could alias a later load as far as the compiler
+      // knows, which would put the loads behind it)
       const V4<double> a1 = ld4(k1 + i), a2 = ld4(k2 + i), a3 = ld4(k3 + i), yy = ld4(y + i), yn = ld4(ynew + i);
+      st4(kout + i, g);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const double E = h * (-5.0 / 72.0 * a1.v[q] + 1.0 / 12.0 * a2.v[q] + 1.0 / 9.0 * a3.v[q] - 0.125 * g.v[q]);
@@ -557,6 +594,7 @@ struct EpiFinal : EpiBase<T> {
         this->accmax = fmax(this->accmax, r);
       }
     } else {
+      st4(kout + i, g);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (!isfinite(g.v[q])) this->accmax = 1.0;

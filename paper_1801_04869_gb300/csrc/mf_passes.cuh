@@ -30,6 +30,21 @@ __device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
   return v;
 }
 
+// Asynchronous copies global -> shared (cp.async): issued without a register round trip,
+// complete at cp_async_wait (this thread's groups; a CTA barrier after it makes every thread's
+// copies visible).  gather_async issues value e from src[goff(e)] to sm[sp(soff(e))] for
+// e < total as one group.
+__device__ __forceinline__ void cp_async_c2(C2<float>* s, const C2<float>* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_c2(C2<double>* s, const C2<double>* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 // Inverse-transform along x the half spectra of rows [2 pr, 2 pr + 1] of NIN fields, packed
 // as complex lines a + i b (Hermitian symmetry of real rows): returns the shared buffer (sm or
 // sm2) holding the rows, row 2pr in .x and row 2pr+1 in .y.  Global element (f, kx, row r)
@@ -56,6 +71,46 @@ __device__ __forceinline__ C2<T>* rows_gather_inverse(C2<T>* sm, C2<T>* sm2, con
   const int l0 = P.lgr(0);
   fft_first_io_any<T, +1>(l0, lgx, NIN * npair, ld, sm, grp);
   return fft_lines_from<T, +1>(sm, sm2, lgx, NIN * npair, twx, 1, grp);
+}
+
+// The same inverse transform from a staged copy of the half spectra in shared memory (element
+// (f, kx, row r) at position sp((f (nx/2 + 1) + kx) rb + r), rb = 2 npair), written by
+// stage_rows_async; the staging buffer is free again when this returns.
+// after_first() runs (in every thread) once the first stage has read the staging buffer.
+template <typename T, int NIN, class AfterFirst>
+__device__ __forceinline__ C2<T>* rows_inverse_staged(const C2<T>* stg, C2<T>* sm, C2<T>* sm2, int npair,
+                                                      int lgpair, int lgx, const C2<T>* __restrict__ twx,
+                                                      AfterFirst after_first) {
+  const int nx = 1 << lgx, half = nx >> 1, rb = 2 * npair;
+  C2<T>* const S = dsm<T>();
+  const int st = dsm_off(stg);
+  auto ld = [=](int line, int m) -> C2<T> {
+    const int f = line >> lgpair, pr = line & (npair - 1);
+    const int k = m <= half ? m : nx - m;
+    const int e = (f * (half + 1) + k) * rb + 2 * pr;      // even: the pair shares a padding group
+    const C2<T> A = S[st + sp(e)], B = S[st + sp(e) + 1];
+    if (k == 0 || k == half) return C2<T>{A.x, B.x};
+    if (m < half) return C2<T>{A.x - B.y, A.y + B.x};          // A + i B
+    return C2<T>{A.x + B.y, B.x - A.y};                         // conj(A) + i conj(B)
+  };
+  const FftPlan P = fft_plan<T>(lgx);
+  fft_first_io_any<T, +1>(P.lgr(0), lgx, NIN * npair, ld, sm);
+  after_first();
+  return fft_lines_from<T, +1>(sm, sm2, lgx, NIN * npair, twx, 1);
+}
+// Issue (cp.async, one group) the copy of the half spectra rows [0, rb) of NIN fields, global
+// element (f, kx, r) at src + f fstride + kx kstride + r, into the staging layout above.
+template <typename T, int NIN>
+__device__ __forceinline__ void stage_rows_async(C2<T>* stg, const C2<T>* src, long long fstride,
+                                                 long long kstride, int rb, int lgx) {
+  const int nk = (1 << (lgx - 1)) + 1;
+  const int per_f = nk * rb;
+  for (int e = threadIdx.x; e < NIN * per_f; e += NT) {
+    const int f = e / per_f, rest = e - f * per_f;
+    const int k = rest / rb, r = rest - k * rb;
+    cp_async_c2(stg + sp(e), src + f * fstride + (long long)k * kstride + r);
+  }
+  cp_async_commit();
 }
 
 // Forward-transform NOUT fields of packed row pairs (in `sm_in`, second buffer `sm2`) along x
@@ -117,21 +172,6 @@ __device__ __forceinline__ void lines_store(const C2<T>* sm, C2<T>* dst, long lo
   __syncthreads();
 }
 
-// Asynchronous copies global -> shared (cp.async): issued without a register round trip,
-// complete at cp_async_wait (this thread's groups; a CTA barrier after it makes every thread's
-// copies visible).  gather_async issues value e from src[goff(e)] to sm[sp(soff(e))] for
-// e < total as one group.
-__device__ __forceinline__ void cp_async_c2(C2<float>* s, const C2<float>* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
-               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_c2(C2<double>* s, const C2<double>* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-               :: "r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 template <typename T, class GOff, class SOff>
 __device__ __forceinline__ void gather_async(C2<T>* sm, const C2<T>* src, int total, GOff goff, SOff soff) {
   for (int e = threadIdx.x; e < total; e += NT) cp_async_c2(sm + sp(soff(e)), src + goff(e));

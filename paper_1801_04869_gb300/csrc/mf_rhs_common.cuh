@@ -73,6 +73,10 @@ struct EpiBase {
   Acc acc = 0, accmax = 0;
   Acc acc2 = 0;                 // a second sum (rows() with a second slot)
   bool is_max = false;
+  // kPair: the epilogue also has pair(ia, ib, ...) for the two rows of a cell pair, which issues
+  // every load of both before any store (a store may alias a later load as far as the compiler
+  // knows, so two separate calls would wait for the first call's loads before the second's)
+  static constexpr bool kPair = false;
 };
 
 struct RhsOut {
