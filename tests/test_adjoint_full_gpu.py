@@ -10,7 +10,9 @@ library's own FP64 adaptive run and checked against the stored target (counts, n
   directions d = jc z.  FP64 transforms to 1e-8; FP32 transforms to the tolerance derived below.
 * Against central differences of the GPU's own FP64 map (eps = 1e-4, relative for jc, absolute
   for the knot values) for 8 of the 32 cells, every knot and both directions: the map is
-  deterministic (fixed reduction order), so the differences resolve the gradient to ~1e-6.
+  deterministic (fixed reduction order), so rounding does not limit the differences; their
+  truncation error O(eps^2) does (3e-5 relative on the first knot, where h_e starts): all to
+  1e-4 relative (the deviations are printed).
 
 FP32 tolerance: every right-hand side of the FP32 form is within 2e-4 of FP64 (relative L2), and
 the gradient of a solve of ~800 steps sums ~2400 vector-Jacobian products and as many forward
@@ -75,14 +77,18 @@ def _target(ref):
 
 
 def _compare(ref, wl, L, cb, vb):
+    """Relative deviations from the stored gradient.  A directional derivative <dL/djc, d> over
+    all cells with random signs cancels to a small fraction of |dL/djc| |d|, so its deviation is
+    measured against that bound (Cauchy-Schwarz), not against its own small value."""
     cells = [tuple(c) for c in ref["cells"]]
     cbv = np.array([cb[iy, ix] for iy, ix in cells])
     dirs = [wl.jc_map * W.rng(s).standard_normal(wl.jc_map.shape) for s in ref["direction_seeds"]]
     dd = np.array([float((cb * d).sum()) for d in dirs])
+    scale = np.array([ref["jcbar_l2"] * float(np.linalg.norm(d)) for d in dirs])
     return {"loss": abs(L - ref["loss"]) / abs(ref["loss"]),
             "knots": float(np.linalg.norm(np.array(vb) - ref["knots_bar"]) / np.linalg.norm(ref["knots_bar"])),
             "cells": float(np.linalg.norm(cbv - ref["jcbar_cells"]) / np.linalg.norm(ref["jcbar_cells"])),
-            "directional": float(np.max(np.abs(dd - ref["directional"]) / np.abs(ref["directional"]))),
+            "directional": float(np.max(np.abs(dd - ref["directional"]) / scale)),
             "l2": abs(float(np.linalg.norm(cb)) - ref["jcbar_l2"]) / ref["jcbar_l2"]}
 
 
@@ -112,7 +118,7 @@ def test_gradient_matches_central_differences_of_the_gpu_map():
         return p.mf_film_solve_gradient(g0, target, steps, counts, C, grad=False)[0]
 
     assert loss() == L0                                        # the map is deterministic
-    worst = 0.0
+    worst = worst_k = 0.0
     for iy, ix in [tuple(c) for c in ref["cells"][:FD_CELLS]]:
         dj = EPS * float(wl.jc_map[iy, ix])
         e = torch.zeros_like(jc)
@@ -125,10 +131,14 @@ def test_gradient_matches_central_differences_of_the_gpu_map():
         up[k] += EPS
         dn[k] -= EPS
         fd = (loss(knots=up) - loss(knots=dn)) / (2 * EPS)
-        assert abs(fd - vb[k]) <= 1e-5 * abs(fd) + 1e-7 * np.abs(vb).max(), (k, fd, vb[k])
+        worst_k = max(worst_k, abs(fd - vb[k]) / abs(fd))
+        assert abs(fd - vb[k]) <= 1e-4 * abs(fd) + 1e-7 * np.abs(vb).max(), (k, fd, vb[k])
+    worst_d = 0.0
     for s in ref["direction_seeds"]:
         d = torch.as_tensor(wl.jc_map * W.rng(s).standard_normal(wl.jc_map.shape), device="cuda")
         fd = (loss(jc + EPS * d) - loss(jc - EPS * d)) / (2 * EPS)
         an = float((cb * d.cpu().numpy()).sum())
-        assert abs(fd - an) <= 1e-6 * abs(fd), (s, fd, an)
-    print(f"central differences: worst cell deviation {worst:.2e}")
+        worst_d = max(worst_d, abs(fd - an) / abs(fd))
+        assert abs(fd - an) <= 1e-4 * abs(fd), (s, fd, an)
+    print(f"central differences: worst relative deviation cells {worst:.2e}, knots {worst_k:.2e}, "
+          f"directions {worst_d:.2e}")
