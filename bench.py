@@ -143,12 +143,14 @@ def _oracle_problem(wl):
                        iter_tol=wl.iter_tol, iter_max=wl.iter_max, lam=wl.lam)
 
 
-def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128):
+def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128, tune: bool = True):
     """Secondary line: the 3D cube (n_grid/2 cells per side in n_grid^3), FP32 transforms,
-    after mf_autotune has picked the work-item shape and launch width (reported beside it)."""
+    after mf_autotune has picked the work-item shape and launch width (reported beside it;
+    tune=False keeps the size rules' choice).  The warm-up and the timed steps are one
+    persistent launch each."""
     wl = W.cube_bulk(n_grid, precision=1)
     p = native.from_workload(wl)
-    tune = p.mf_autotune(reps=2, force_iters=2)      # transform work does not depend on the values
+    tune = p.mf_autotune(reps=2, force_iters=2) if tune else None   # transform work does not depend on the values
     p.mf_set_state(0.0, None, h=1e-3)
     p.mf_advance(1.0, max_attempts=warmup)
     torch.cuda.synchronize()
@@ -551,7 +553,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the bulk and full-ramp legs")
     ap.add_argument("--grid", type=int, default=2048, help="film grid (2048 is the benchmark)")
-    ap.add_argument("--only", choices=["batch", "adjoint", "ramps", "fp64", "cufft"],
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--only bulk: keep the size rules' item shape (no mf_autotune launches)")
+    ap.add_argument("--only", choices=["batch", "adjoint", "ramps", "fp64", "cufft", "bulk"],
                     help="run one secondary leg alone")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max-side", type=int, default=512)
@@ -593,6 +597,13 @@ def main():
     if args.only == "cufft":
         if rank == 0:
             print(json.dumps(cufft_leg(torch)))
+        return
+    if args.only == "bulk":
+        # the cube leg alone: --grid 128 or 256 (the cube has half the grid's cells per side)
+        if rank == 0:
+            print(json.dumps(bulk_leg(native, W, torch, steps=args.steps, warmup=args.warmup,
+                                      n_grid=args.grid if args.grid <= 512 else 128,
+                                      tune=not args.no_tune)))
         return
     dist = None
     if world > 1:
