@@ -159,7 +159,7 @@ def test_frozen_map_is_the_adaptive_solve():
     on an h_e knot (15 of the 794): there the integrator evaluates a k4 that the next step
     discards (h_e_dot jumps) and warm-starts the recomputed k1 from it, while the frozen map,
     which has no k4 call, warm-starts k1 from k3; with the same iteration counts the two starts
-    leave differences at the level of the stop tolerance."""
+    leave differences at the level of the stop tolerance (measured 7.6e-6 relative L2)."""
     ref = _stored()
     wl = W.adjoint_film(ref["grid"][0], precision=0, T=ref["T"])
     pa = native.from_workload(wl)
@@ -176,4 +176,4 @@ def test_frozen_map_is_the_adaptive_solve():
                              grad=False, hz_out=hz_f)
     err = float(torch.linalg.norm(hz_f - hz_a) / torch.linalg.norm(hz_a))
     print(f"frozen forward against the adaptive run: h_z(T) relative L2 {err:.2e}")
-    assert err < 1e-4, err
+    assert err < 3e-5, err
