@@ -22,6 +22,11 @@ namespace mf {
 
 enum Op3 { OP3_CURL = 0, OP3_CURLNEG = 1, OP3_PHI = 2 };
 
+// y and z lines of at least 2^TMA_MIN_LG points are staged by bulk copies (tensor memory
+// accelerator); shorter ones by per-thread cp.async into a rotating third buffer, which issues
+// the next item's gather earlier (measured faster for the 128-point lines of a 128^3 grid)
+constexpr int TMA_MIN_LG = 8;
+
 // raw pointers and sizes the x-pass epilogues need, held by value (registers)
 template <typename T>
 struct BulkPtrs {
@@ -188,6 +193,49 @@ struct Bulk {
     }
   }
 
+  // ---- passes whose items are contiguous lines: item it's `nl` lines of length 2^lg (line l
+  // at src(it, l)) are copied by the tensor memory accelerator (cp.async.bulk) into the third
+  // buffer, line l at l (2^lg + 2) (the two spare values per line shift successive lines by
+  // four banks), completion counted on the CTA's mbarrier.  work(it, after_first) runs the item
+  // and calls after_first() once its first transform stage has read the staging buffer; that
+  // issues the next item's copies, which then land while this item finishes. ----
+  template <class Src, class Work>
+  __device__ __forceinline__ void tma_lines(int nitems, int nl, int lg, Src src, Work work) {
+    unsigned long long* const bar = &sh.tma_bar;
+    const int stride = (1 << lg) + 2;
+    const unsigned bytes = (unsigned)sizeof(C2<T>) << lg;
+    C2<T>* const stg = sm3;
+    auto issue = [&](int it) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, bytes * (unsigned)nl);
+        for (int l = 0; l < nl; ++l) bulk_g2s(stg + l * stride, src(it, l), bytes, bar);
+      }
+    };
+    unsigned parity = sh.tma_parity;
+    int it = (int)blockIdx.x;
+    if (it < nitems) issue(it);
+    for (; it < nitems; it += (int)gridDim.x) {
+      mbar_wait(bar, parity, d.gb, d.barrier_ns);
+      parity ^= 1u;
+      const int nxt = it + (int)gridDim.x;
+      work(it, [&] { if (nxt < nitems) issue(nxt); });
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh.tma_parity = parity;
+    __syncthreads();
+  }
+  // first (inverse or forward) transform stage of nl staged lines into `out`, then after_first()
+  template <int DIR, class AfterFirst>
+  __device__ __forceinline__ void first_from_stage(int lg, int nl, C2<T>* out, AfterFirst after_first) {
+    C2<T>* const S = dsm<T>();
+    const int st = dsm_off(sm3);
+    const int stride = (1 << lg) + 2;
+    const FftPlan P = fft_plan<T>(lg);
+    fft_first_io_any<T, DIR>(P.lgr(0), lg, nl, [=](int line, int pos) { return S[st + line * stride + pos]; }, out);
+    after_first();
+  }
+
   // ---- y pass, forward: S1[c][z][kx][:] -> S2[c][kx][:][z] for z in [z0, z0 + zs) ----
   __device__ __noinline__ void yfwd() {
     const int ny = this->ny, nz = this->nz, lgy = this->lgy, nkx = this->nkx, zs = this->zs;
@@ -197,6 +245,28 @@ struct Bulk {
     const C2<T>* const twy = this->twy;
     const int per_kx = nz / zs;
     const int nl = 3 * zs;
+    // transposed write of the item's transformed lines (X: line c zs + dz, wavenumber ky)
+    auto scatter = [=](const C2<T>* X, int kx, int z0) {
+      for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
+        const int dz = e % zs, rest = e / zs;
+        const int ky = rest & (ny - 1), c = rest >> lgy;
+        S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz] = X[sp(((c * zs + dz) << lgy) + ky)];
+      }
+      __syncthreads();
+    };
+    if (lgy >= TMA_MIN_LG) {
+      tma_lines(nkx * per_kx, nl, lgy,
+          [=](int it, int l) {
+            const int kx = it / per_kx, z0 = (it % per_kx) * zs;
+            const int c = l / zs, dz = l - c * zs;
+            return (const C2<T>*)(S1 + c * nspec + ((long long)(z0 + dz) * nkx + kx) * ny);
+          },
+          [&](int it, auto after_first) {
+            first_from_stage<-1>(lgy, nl, sm, after_first);
+            scatter(fft_lines_from<T, -1>(sm, sm2, lgy, nl, twy, 1), it / per_kx, (it % per_kx) * zs);
+          });
+      return;
+    }
     pipelined(nkx * per_kx,
         [=](int it, C2<T>* buf) {
           const int kx = it / per_kx, z0 = (it % per_kx) * zs;
@@ -209,14 +279,7 @@ struct Bulk {
               [](int e) { return e; });
         },
         [=](int it, C2<T>* a, C2<T>* b) {
-          const int kx = it / per_kx, z0 = (it % per_kx) * zs;
-          const C2<T>* X = fft_lines<T, -1>(a, b, lgy, nl, twy);
-          for (int e = threadIdx.x; e < (nl << lgy); e += NT) {
-            const int dz = e % zs, rest = e / zs;
-            const int ky = rest & (ny - 1), c = rest >> lgy;
-            S2[c * nspec + ((long long)kx * ny + ky) * nz + z0 + dz] = X[sp(((c * zs + dz) << lgy) + ky)];
-          }
-          __syncthreads();
+          scatter(fft_lines<T, -1>(a, b, lgy, nl, twy), it / per_kx, (it % per_kx) * zs);
         });
   }
   // ---- y pass, inverse: S2 -> S1 ----
@@ -265,51 +328,67 @@ struct Bulk {
     const int per_kx = ny / P;
     const T s = (T)1 / (T)ncell;
     const int pl = P << lgz;                         // values per component
+    // multiplier, inverse transform and write of an item whose forward transform is in X (Y:
+    // the other buffer)
+    auto finish = [=](C2<T>* X, C2<T>* Y, int kx, int ky0) {
+      const long long base = ((long long)kx * ny + ky0) * nz;
+      const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
+      const T kxo = kx == half ? (T)0 : kxv;
+      for (int e = threadIdx.x; e < pl; e += NT) {
+        const int p = e >> lgz, kz = e & (nz - 1);
+        const int ky = ky0 + p;
+        const T kyv = ldg_tab(&ktab[nkx + ky]), kzv = ldg_tab(&ktab[nkx + ny + kz]);
+        const T kyo = ky == ny / 2 ? (T)0 : kyv;
+        const T kzo = kz == nz / 2 ? (T)0 : kzv;
+        const C2<T> va = X[sp(e)], vb = X[sp(pl + e)], vc = X[sp(2 * pl + e)];
+        // cross product k x v with the odd (Nyquist-free) wavenumbers
+        C2<T> cx = {kyo * vc.x - kzo * vb.x, kyo * vc.y - kzo * vb.y};
+        C2<T> cy = {kzo * va.x - kxo * vc.x, kzo * va.y - kxo * vc.y};
+        C2<T> cz = {kxo * vb.x - kyo * va.x, kxo * vb.y - kyo * va.y};
+        T f;
+        if (op == OP3_PHI) {
+          const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+          f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
+        } else {
+          const T G = gx * ldg_tab(&gtab[nkx + ky]) * ldg_tab(&gtab[nkx + ny + kz]);
+          f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
+        }
+        X[sp(e)] = cmul_si(cscale(cx, f), 1);
+        X[sp(pl + e)] = cmul_si(cscale(cy, f), 1);
+        X[sp(2 * pl + e)] = cmul_si(cscale(cz, f), 1);
+      }
+      __syncthreads();
+      const C2<T>* Z = fft_lines<T, +1>(X, Y, lgz, 3 * P, twz);
+      for (int e = threadIdx.x; e < 3 * pl; e += NT) {
+        const int c = e / pl, r = e - c * pl;
+        S2[c * nspec + base + r] = Z[sp(e)];
+      }
+      __syncthreads();
+    };
+    if (lgz >= TMA_MIN_LG) {
+      tma_lines(nkx * per_kx, 3 * P, lgz,
+          [=](int it, int l) {
+            const int kx = it / per_kx, ky0 = (it % per_kx) * P;
+            const int c = l / P, p = l - c * P;
+            return (const C2<T>*)(S2 + c * nspec + ((long long)kx * ny + ky0 + p) * nz);
+          },
+          [&](int it, auto after_first) {
+            first_from_stage<-1>(lgz, 3 * P, sm, after_first);
+            C2<T>* X = fft_lines_from<T, -1>(sm, sm2, lgz, 3 * P, twz, 1);
+            finish(X, X == sm ? sm2 : sm, it / per_kx, (it % per_kx) * P);
+          });
+      return;
+    }
     pipelined(nkx * per_kx,
         [=](int it, C2<T>* buf) {
-          const int kx = it / per_kx, ky0 = (it % per_kx) * P;
-          const long long base = ((long long)kx * ny + ky0) * nz;
+          const long long base = ((long long)(it / per_kx) * ny + (it % per_kx) * P) * nz;
           gather_async<T>(buf, S2, 3 * pl,
               [=](int e) { const int c = e / pl; return c * nspec + base + (e - c * pl); },
               [](int e) { return e; });
         },
         [=](int it, C2<T>* a, C2<T>* b) {
-          const int kx = it / per_kx, ky0 = (it % per_kx) * P;
-          const long long base = ((long long)kx * ny + ky0) * nz;
           C2<T>* X = fft_lines<T, -1>(a, b, lgz, 3 * P, twz);
-          C2<T>* Y = X == a ? b : a;
-          const T kxv = ldg_tab(&ktab[kx]), gx = ldg_tab(&gtab[kx]);
-          const T kxo = kx == half ? (T)0 : kxv;
-          for (int e = threadIdx.x; e < pl; e += NT) {
-            const int p = e >> lgz, kz = e & (nz - 1);
-            const int ky = ky0 + p;
-            const T kyv = ldg_tab(&ktab[nkx + ky]), kzv = ldg_tab(&ktab[nkx + ny + kz]);
-            const T kyo = ky == ny / 2 ? (T)0 : kyv;
-            const T kzo = kz == nz / 2 ? (T)0 : kzv;
-            const C2<T> va = X[sp(e)], vb = X[sp(pl + e)], vc = X[sp(2 * pl + e)];
-            // cross product k x v with the odd (Nyquist-free) wavenumbers
-            C2<T> cx = {kyo * vc.x - kzo * vb.x, kyo * vc.y - kzo * vb.y};
-            C2<T> cy = {kzo * va.x - kxo * vc.x, kzo * va.y - kxo * vc.y};
-            C2<T> cz = {kxo * vb.x - kyo * va.x, kxo * vb.y - kyo * va.y};
-            T f;
-            if (op == OP3_PHI) {
-              const T k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-              f = k2 > (T)0 ? s / k2 : (T)0;                   // Eq. 17
-            } else {
-              const T G = gx * ldg_tab(&gtab[nkx + ky]) * ldg_tab(&gtab[nkx + ny + kz]);
-              f = (op == OP3_CURL ? G : -G) * s;               // smoothed curl
-            }
-            X[sp(e)] = cmul_si(cscale(cx, f), 1);
-            X[sp(pl + e)] = cmul_si(cscale(cy, f), 1);
-            X[sp(2 * pl + e)] = cmul_si(cscale(cz, f), 1);
-          }
-          __syncthreads();
-          const C2<T>* Z = fft_lines<T, +1>(X, Y, lgz, 3 * P, twz);
-          for (int e = threadIdx.x; e < 3 * pl; e += NT) {
-            const int c = e / pl, r = e - c * pl;
-            S2[c * nspec + base + r] = Z[sp(e)];
-          }
-          __syncthreads();
+          finish(X, X == a ? b : a, it / per_kx, (it % per_kx) * P);
         });
   }
 
@@ -620,6 +699,8 @@ __global__ void __launch_bounds__(NT, 2) bulk_kernel(const Desc* __restrict__ dg
     sh.warm_valid = st->warm_valid;
     sh.bar_passed = 0;
     sh.A_prev = 0.0;
+    sh.tma_parity = 0;
+    mbar_init(&sh.tma_bar);
   }
   if (threadIdx.x == 0) new (objraw) Bulk<T>(d, sm, sh);
   __syncthreads();

@@ -30,6 +30,45 @@ __device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
   return v;
 }
 
+// Bulk copies global -> shared by the tensor memory accelerator (cp.async.bulk, the 1-D form):
+// one thread arms the CTA's mbarrier with the transaction bytes and issues the copies; every
+// thread then waits on the barrier's phase, which completes when all bytes have landed.
+// Addresses 16-byte aligned, sizes multiples of 16 bytes.  A wait that exceeds the time limit
+// raises the grid barrier's abort flag, so the launch stops at its next grid barrier.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// generic-proxy accesses (earlier stores to global by any CTA, earlier reads of the staging
+// buffer) ordered before the async-proxy copies issued after it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, GridBarrier* gb,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return;
+  const unsigned long long lim = limit_ns ? limit_ns : BARRIER_LIMIT_NS;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > lim) {
+      atomicOr(&gb->count, BARRIER_ABORT);
+      return;
+    }
+  }
+}
+
 // Asynchronous copies global -> shared (cp.async): issued without a register round trip,
 // complete at cp_async_wait (this thread's groups; a CTA barrier after it makes every thread's
 // copies visible).  gather_async issues value e from src[goff(e)] to sm[sp(soff(e))] for

@@ -29,6 +29,8 @@ struct Shared {
   double q11;                    // (2D) sum over free space of q1 (from the solver state)
   int attempt_first;             // (2D) the next right-hand side is the first of a step attempt
   unsigned long long bar_passed;  // grid barriers passed in this launch (thread 0)
+  unsigned long long tma_bar;     // (3D) mbarrier of the bulk copies into the staging buffer
+  unsigned tma_parity;            // (3D) phase parity the next wait on tma_bar expects
 };
 
 // ------------------------------------------------------------------------------------------
