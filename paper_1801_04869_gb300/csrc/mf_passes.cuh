@@ -34,7 +34,9 @@ __device__ __forceinline__ CPair<double> ld_pair_stream(const C2<double>* p) {
 // one thread arms the CTA's mbarrier with the transaction bytes and issues the copies; every
 // thread then waits on the barrier's phase, which completes when all bytes have landed.
 // Addresses 16-byte aligned, sizes multiples of 16 bytes.  A wait that exceeds the time limit
-// raises the grid barrier's abort flag, so the launch stops at its next grid barrier.
+// raises the grid barrier's abort flag, so the launch stops at its next grid barrier, and then
+// keeps waiting (up to the default barrier limit) so that no copy is still landing in shared
+// memory when the CTA leaves.
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(bar)) : "memory");
@@ -61,11 +63,14 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned pari
   if (mbar_try_wait(bar, parity)) return;
   const unsigned long long lim = limit_ns ? limit_ns : BARRIER_LIMIT_NS;
   const unsigned long long t0 = globaltimer_ns();
+  bool raised = false;
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer_ns() - t0 > lim) {
+    const unsigned long long el = globaltimer_ns() - t0;
+    if (!raised && el > lim) {
       atomicOr(&gb->count, BARRIER_ABORT);
-      return;
+      raised = true;
     }
+    if (el > lim + BARRIER_LIMIT_NS) return;       // the copies never landed: give up
   }
 }
 

@@ -102,6 +102,24 @@ def test_rhs_fp64_variants(case):
     _rhs_pair(wl, h, [0.05, 0.4], force=2)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("dims", [(32, 256, 256), (16, 512, 256)])
+def test_rhs_with_bulk_copied_lines(dims, precision, tol):
+    """y and z lines of 256 or more points arrive by bulk copies (tensor memory accelerator) into
+    the staging buffer, shorter ones by per-thread asynchronous copies: a forced-iteration right-
+    hand side and the current readout on grids that take the bulk copies on one or both axes,
+    in both precisions (FP64: 16-byte values, twice the bytes per line)."""
+    nx, ny, nz = dims
+    wl = bulk_workload(nx, ny, nz, L=(0.5, 2.0, 2.0), precision=precision, ax=0.3, ay=1.0, az=1.0)
+    h = W.bulk_state(wl.mask, (wl.Lx, wl.Ly, wl.Lz), seed=71, h0=0.3, depth=0.3)
+    _rhs_pair(wl, h, [0.2], force=2, tol=tol)
+    o = oracle_of(wl)
+    p = native.from_workload(wl)
+    out = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    p.mf_readout(native.MF_READ_J, out=out, t=0.2, y=dev(h))
+    assert rel_l2(out.cpu().numpy(), o.current(h)) < (1e-13 if precision == 0 else 2e-6)
+
+
 def test_rhs_no_free_space_single_pass():
     wl = bulk_workload(16, 16, 16, ax=5.0, ay=5.0, az=5.0)
     assert (wl.mask == 1).all()

@@ -31,7 +31,7 @@ def _nan_film(**kw):
     return wl, g
 
 
-@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("dim", [2, 3, "3_bulk_copies"])
 def test_barrier_wait_that_runs_out_returns_a_status(dim):
     """A grid-barrier time limit of 1 ns makes the first CTA to reach a barrier give up before
     the others arrive: the launch raises its abort flag, every CTA leaves, and the call returns
@@ -41,6 +41,13 @@ def test_barrier_wait_that_runs_out_returns_a_status(dim):
     if dim == 2:
         wl = film_workload(128, 128, precision=0, ax=1.0, ay=1.0)
         y0 = W.film_state(wl.mask, wl.Lx, wl.Ly, seed=62, amplitude=0.4)
+    elif dim == "3_bulk_copies":
+        # y and z lines of 256 points: their gathers are bulk copies on an mbarrier, whose
+        # waits give up at the same limit and then drain the copies before the CTA leaves
+        m = W.bulk_mask(16, 256, 256, 0.5, 2.0, 2.0, "box", ax=0.3, ay=1.0, az=1.0)
+        wl = W.Workload("box_16x256x256", 3, 16, 256, 256, 0.5, 2.0, 2.0, m, n=25.0, rho_out=5.0,
+                        precision=0, t0=0.0, t1=1.0, he_knots=((0.0, 1.0), (0.0, 0.5)), iter_tol=1e-4)
+        y0 = W.bulk_state(m, (0.5, 2.0, 2.0), seed=64, h0=0.3, depth=0.3)
     else:
         m = W.bulk_mask(32, 32, 32, 1.0, 1.0, 1.0, "box", ax=0.5, ay=0.5, az=0.5)
         wl = W.Workload("cube32", 3, 32, 32, 32, 1.0, 1.0, 1.0, m, n=25.0, rho_out=5.0, precision=0,
