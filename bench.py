@@ -143,11 +143,13 @@ def _oracle_problem(wl):
                        iter_tol=wl.iter_tol, iter_max=wl.iter_max, lam=wl.lam)
 
 
-def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128, tune: bool = True):
+def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 128, tune: bool = True,
+             cufft: bool = True):
     """Secondary line: the 3D cube (n_grid/2 cells per side in n_grid^3), FP32 transforms,
     after mf_autotune has picked the work-item shape and launch width (reported beside it;
     tune=False keeps the size rules' choice).  The warm-up and the timed steps are one
-    persistent launch each."""
+    persistent launch each; with cufft, cuFFT's transform floor of one vector round trip on the
+    same grid is timed afterwards beside the library's time per vector round trip."""
     wl = W.cube_bulk(n_grid, precision=1)
     p = native.from_workload(wl)
     tune = p.mf_autotune(reps=2, force_iters=2) if tune else None   # transform work does not depend on the values
@@ -171,6 +173,8 @@ def bulk_leg(native, W, torch, steps: int = 6, warmup: int = 2, n_grid: int = 12
             "roofline": {"bound": "hbm", "achieved": alg / sec / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / sec / 1e9 / peak, "peak_kind": kind,
                          "bytes_model": f"(60 + 60 I) M3 per RHS, M3 = {n_grid}^3 x 4 B"},
+            "ms_per_vector_round_trip": 1000.0 * sec / (2 * n_rhs + 2 * n_it),
+            "cufft": cufft3_leg(torch, n_grid) if cufft else None,
             "autotune": tune}
 
 
@@ -465,6 +469,33 @@ def cufft_leg(torch, n: int = 2048, reps: int = 50):
         torch.cuda.synchronize()
         out[f"ms_per_round_trip_{name}"] = e0.elapsed_time(e1) / reps
     return out
+
+
+def cufft3_leg(torch, n: int, reps: int = 10):
+    """Reference point only (the library never calls it): the transform floor of one vector
+    round trip of the bulk solver through torch.fft (cuFFT), irfftn(M * rfftn(h)) of the three
+    components of an n^3 FP32 field with one real multiplier (a lower bound on the pointwise work
+    of a spectral curl), CUDA-event timed after warm-up."""
+    x = torch.randn(3, n, n, n, device="cuda", dtype=torch.float32)
+    mult = torch.rand(n, n, n // 2 + 1, device="cuda", dtype=torch.float32)
+
+    def rt():
+        return torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)) * mult, s=(n, n, n), dim=(1, 2, 3))
+    for _ in range(3):
+        rt()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rt()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, mult
+    torch.cuda.empty_cache()
+    return {"grid": [n, n, n], "ms_per_vector_round_trip_f32": ms,
+            "note": "torch.fft (cuFFT) forward and inverse of 3 components with one pointwise "
+                    "multiplier; timed beside the library as a reference point only"}
 
 
 def combine_ranks(dist, sec: float, n_rhs: int, e2e_rate: float, device):
