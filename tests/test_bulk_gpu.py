@@ -120,6 +120,27 @@ def test_rhs_with_bulk_copied_lines(dims, precision, tol):
     assert rel_l2(out.cpu().numpy(), o.current(h)) < (1e-13 if precision == 0 else 2e-6)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("dims", [(512, 64, 32), (16, 16, 512)])
+def test_rhs_at_the_maximum_axis_length(dims, precision, tol):
+    """512 points, the largest axis the bulk path accepts, along x (x-pass items of 4 rows of
+    three fields, 257-point half spectra) and along z (z lines of 512 points by bulk copies):
+    a forced-iteration right-hand side and the current readout against the oracle."""
+    nx, ny, nz = dims
+    L = (2.0, 0.25, 0.125) if nx == 512 else (0.125, 0.125, 2.0)
+    ext = dict(ax=1.0, ay=0.1, az=0.05) if nx == 512 else dict(ax=0.08, ay=0.06, az=1.0)
+    wl = bulk_workload(nx, ny, nz, L=L, precision=precision, **ext)
+    h = W.bulk_state(wl.mask, (wl.Lx, wl.Ly, wl.Lz), seed=73, h0=0.3, depth=0.05, noise=0.01)
+    _rhs_pair(wl, h, [0.2], force=2, tol=tol)
+    o = oracle_of(wl)
+    p = native.from_workload(wl)
+    if nx == 512:
+        assert p.mf_get_info()["rows_per_item"] == 4
+    out = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    p.mf_readout(native.MF_READ_J, out=out, t=0.2, y=dev(h))
+    assert rel_l2(out.cpu().numpy(), o.current(h)) < (1e-13 if precision == 0 else 2e-6)
+
+
 def test_rhs_no_free_space_single_pass():
     wl = bulk_workload(16, 16, 16, ax=5.0, ay=5.0, az=5.0)
     assert (wl.mask == 1).all()
