@@ -171,7 +171,9 @@ mf_status mf_advance(mf_problem* pb, double t_target, long long max_attempts);
    waited for.  Batching has no counterpart in the paper: it is how many independent
    magnetization problems (a parameter or geometry sweep) share one GPU.  statuses (may be
    NULL) receives each problem's status; the return value is the first non-OK one (MF_OK if
-   all succeeded).  pbs must not repeat a problem.  Returns when every problem has finished. */
+   all succeeded).  n = 0 does nothing and returns MF_OK.  MF_ERR_ARG, before any work: pbs or
+   t_targets NULL, n < 0, a NULL or a repeated problem.  Returns when every problem has
+   finished. */
 mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_targets,
                            long long max_attempts, mf_status* statuses);
 

@@ -665,6 +665,12 @@ mf_status mf_advance_batch(mf_problem* const* pbs, int n, const double* t_target
   if (!pbs || !t_targets || n < 0) return MF_ERR_ARG;
   for (int i = 0; i < n; ++i)
     if (!pbs[i]) return MF_ERR_ARG;
+  {
+    // a repeated problem would run twice at once on one workspace and grid barrier
+    std::vector<mf_problem*> seen(pbs, pbs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return MF_ERR_ARG;
+  }
   std::vector<mf_status> st(n, MF_OK);
   for (int i = 0; i < n; ++i) st[i] = ensure_h(pbs[i], t_targets[i]);
   // films of one device and precision share persistent launches; bulk bodies get one launch

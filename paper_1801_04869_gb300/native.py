@@ -426,7 +426,9 @@ def advance_batch(problems, t_targets, max_attempts: int = 1 << 40):
     r = lib.mf_advance_batch(hs, n, ts, max_attempts, st)
     out = list(st)
     if r != 0:
-        bad = next(i for i, v in enumerate(out) if v != 0)
+        bad = next((i for i, v in enumerate(out) if v != 0), None)
+        if bad is None:          # refused before any problem ran
+            raise MFError(r, "mf_advance_batch refused its arguments (a NULL or repeated problem)")
         raise MFError(r, f"problem {bad}: " + lib.mf_last_error(problems[bad].h).decode())
     return out
 

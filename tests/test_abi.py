@@ -103,6 +103,11 @@ def test_null_and_invalid_arguments_are_refused_without_a_gpu(lib):
     assert lib.mf_checkpoint_save(None, None) == native.MF_ERR_ARG
     assert lib.mf_checkpoint_restore(None, None) == native.MF_ERR_ARG
     assert lib.mf_advance_batch(None, 1, None, 1, None) == native.MF_ERR_ARG
+    none = (ctypes.c_void_p * 1)()
+    tt = (ctypes.c_double * 1)(1.0)
+    assert lib.mf_advance_batch(none, 0, tt, 1, None) == native.MF_OK      # nothing to do
+    assert lib.mf_advance_batch(none, -1, tt, 1, None) == native.MF_ERR_ARG
+    assert lib.mf_advance_batch(none, 1, tt, 1, None) == native.MF_ERR_ARG  # a NULL problem
     assert lib.mf_advance(None, 1.0, 1) == native.MF_ERR_ARG
     assert lib.mf_rhs(None, 0.0, None, None, None) == native.MF_ERR_ARG
     assert lib.mf_get_info(None, None) == native.MF_ERR_ARG

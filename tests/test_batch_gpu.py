@@ -81,3 +81,17 @@ def test_batch_reports_each_status():
         native.advance_batch([good, bad], [0.02, 0.02], max_attempts=200)
     t, _, _ = _state(good, wls[0].nx * wls[0].ny)
     assert t == pytest.approx(0.02, abs=1e-12)
+
+
+def test_batch_refuses_a_repeated_problem_and_runs_nothing():
+    """The same problem twice in one call would run twice at once on one workspace: refused with
+    MF_ERR_ARG before any work (the problem's state is untouched); no problems: nothing to do."""
+    wl = W.film_batch(1, seed=8, max_side=64, precision=1)[0]
+    p = native.from_workload(wl)
+    p.mf_set_state(0.0, None, h=1e-3)
+    with pytest.raises(native.MFError) as e:
+        native.advance_batch([p, p], [0.02, 0.02])
+    assert e.value.status == native.MF_ERR_ARG
+    t, h, _ = _state(p, wl.nx * wl.ny)
+    assert (t, h) == (0.0, 1e-3) and p.mf_get_info()["n_attempts"] == 0
+    assert native.advance_batch([], []) == []
