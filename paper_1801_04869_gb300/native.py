@@ -203,6 +203,36 @@ class Problem:
         self.state_len = nx * ny * (1 if dim == 2 else 3 * p.nz)
 
     # -- helpers -----------------------------------------------------------------------------
+    def _f64(self, t, n: int, name: str) -> ctypes.c_void_p:
+        """Device pointer of `t`, a contiguous float64 tensor of at least n values on the
+        problem's device (None: NULL).  The library takes bare pointers and cannot check a
+        buffer's length, so a short or misplaced tensor is refused here."""
+        if t is None:
+            return ctypes.c_void_p(0)
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64:
+            raise TypeError(f"{name}: a float64 torch tensor is needed, got "
+                            f"{getattr(t, 'dtype', type(t).__name__)}")
+        if not t.is_cuda or t.device.index != self.device.index:
+            raise ValueError(f"{name}: the tensor must be on {self.device}, it is on {t.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: the tensor must be contiguous")
+        if t.numel() < n:
+            raise ValueError(f"{name}: {n} values are needed, the tensor has {t.numel()}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _readout_len(self, what: int) -> int:
+        ncell = self.nx * self.ny * self.nz
+        if what == MF_READ_HZ:
+            return ncell
+        return (2 if self.dim == 2 and what == MF_READ_E else 3) * ncell
+
+    def _blob(self, t, name: str) -> ctypes.c_void_p:
+        n = self.lib.mf_checkpoint_bytes(self.h)
+        if t.numel() * t.element_size() < n or not t.is_contiguous():
+            raise ValueError(f"{name}: a contiguous buffer of {n} bytes is needed")
+        return _dptr(t)
+
     def _check(self, st: int, allow=()):
         if st != MF_OK and st not in allow:
             raise MFError(st, self.lib.mf_last_error(self.h).decode())
@@ -216,7 +246,8 @@ class Problem:
     # -- the C entry points ------------------------------------------------------------------
     def mf_rhs(self, t: float, y, ydot, force_iters: int = 0, seg: int = -2, allow_noconv=False):
         it = ctypes.c_int(0)
-        st = self.lib.mf_rhs_ex(self.h, t, seg, _dptr(y), _dptr(ydot), force_iters, ctypes.byref(it))
+        st = self.lib.mf_rhs_ex(self.h, t, seg, self._f64(y, self.state_len, "y"),
+                                self._f64(ydot, self.state_len, "ydot"), force_iters, ctypes.byref(it))
         self._check(st, allow=(MF_ERR_NOCONV,) if allow_noconv else ())
         return it.value, st
 
@@ -228,11 +259,12 @@ class Problem:
         self._check(self.lib.mf_set_barrier_timeout(self.h, float(seconds)))
 
     def mf_set_state(self, t: float, y=None, h: float = 0.0):
-        self._check(self.lib.mf_set_state(self.h, t, h, _dptr(y)))
+        self._check(self.lib.mf_set_state(self.h, t, h, self._f64(y, self.state_len, "y")))
 
     def mf_get_state(self, y=None):
         t, h = ctypes.c_double(), ctypes.c_double()
-        self._check(self.lib.mf_get_state(self.h, ctypes.byref(t), ctypes.byref(h), _dptr(y)))
+        self._check(self.lib.mf_get_state(self.h, ctypes.byref(t), ctypes.byref(h),
+                                          self._f64(y, self.state_len, "y")))
         return t.value, h.value
 
     def mf_advance(self, t_target: float, max_attempts: int = 1 << 40):
@@ -264,12 +296,13 @@ class Problem:
             if y is None:
                 self._check(self.lib.mf_readout(self.h, what, ptr))
             else:
-                self._check(self.lib.mf_readout_of(self.h, what, t, _dptr(y), ptr))
+                self._check(self.lib.mf_readout_of(self.h, what, t, self._f64(y, self.state_len, "y"), ptr))
             return host
+        dout = self._f64(out, self._readout_len(what), "out")
         if y is None:
-            self._check(self.lib.mf_readout(self.h, what, _dptr(out)))
+            self._check(self.lib.mf_readout(self.h, what, dout))
         else:
-            self._check(self.lib.mf_readout_of(self.h, what, t, _dptr(y), _dptr(out)))
+            self._check(self.lib.mf_readout_of(self.h, what, t, self._f64(y, self.state_len, "y"), dout))
         return out
 
     def mf_get_info(self) -> dict:
@@ -290,13 +323,11 @@ class Problem:
         n = self.lib.mf_checkpoint_bytes(self.h)
         if out is None:
             out = torch.empty(n, dtype=torch.uint8, device=self.device)
-        if out.numel() * out.element_size() < n:
-            raise ValueError(f"checkpoint needs {n} bytes")
-        self._check(self.lib.mf_checkpoint_save(self.h, _dptr(out)))
+        self._check(self.lib.mf_checkpoint_save(self.h, self._blob(out, "out")))
         return out
 
     def mf_checkpoint_restore(self, blob):
-        self._check(self.lib.mf_checkpoint_restore(self.h, _dptr(blob)))
+        self._check(self.lib.mf_checkpoint_restore(self.h, self._blob(blob, "blob")))
 
     def mf_film_outside_vjp(self, v, iters: int, out=None):
         """Cotangents (of h_dot_in as a device tensor, of h_e_dot as a float) of the film's
@@ -305,7 +336,9 @@ class Problem:
         if out is None:
             out = torch.empty_like(v)
         sb = ctypes.c_double(0.0)
-        self._check(self.lib.mf_film_outside_vjp(self.h, iters, _dptr(v), _dptr(out), ctypes.byref(sb)))
+        n = self.state_len
+        self._check(self.lib.mf_film_outside_vjp(self.h, iters, self._f64(v, n, "v"), self._f64(out, n, "out"),
+                                                 ctypes.byref(sb)))
         return out, sb.value
 
     def mf_film_rhs_vjp(self, g, v, iters: int):
@@ -314,8 +347,10 @@ class Problem:
         import torch
         gbar, jcbar = torch.empty_like(v), torch.empty_like(v)
         sb = ctypes.c_double(0.0)
-        self._check(self.lib.mf_film_rhs_vjp(self.h, iters, _dptr(g), _dptr(v), _dptr(gbar),
-                                             _dptr(jcbar), ctypes.byref(sb)))
+        n = self.state_len
+        self._check(self.lib.mf_film_rhs_vjp(self.h, iters, self._f64(g, n, "g"), self._f64(v, n, "v"),
+                                             self._f64(gbar, n, "gbar"), self._f64(jcbar, n, "jcbar"),
+                                             ctypes.byref(sb)))
         return gbar, jcbar, sb.value
 
     def mf_film_rhs_vjp_warm(self, g, v, iters: int, wbar_out=None):
@@ -324,9 +359,11 @@ class Problem:
         import torch
         gbar, jcbar, wbar = torch.empty_like(v), torch.empty_like(v), torch.empty_like(v)
         sb = ctypes.c_double(0.0)
-        self._check(self.lib.mf_film_rhs_vjp_warm(self.h, iters, _dptr(g), _dptr(v), _dptr(wbar_out),
-                                                  _dptr(gbar), _dptr(jcbar), _dptr(wbar),
-                                                  ctypes.byref(sb)))
+        n = self.state_len
+        self._check(self.lib.mf_film_rhs_vjp_warm(self.h, iters, self._f64(g, n, "g"), self._f64(v, n, "v"),
+                                                  self._f64(wbar_out, n, "wbar_out"),
+                                                  self._f64(gbar, n, "gbar"), self._f64(jcbar, n, "jcbar"),
+                                                  self._f64(wbar, n, "wbar"), ctypes.byref(sb)))
         return gbar, jcbar, wbar, sb.value
 
     def mf_film_solve_gradient(self, g0, target, steps, iters, ckpt_every: int = 20, warm0=None,
@@ -351,14 +388,17 @@ class Problem:
         kb = (ctypes.c_double * max(K, 1))() if grad else None
         wb = torch.empty_like(g0) if (grad and warm0_grad) else None
         loss = ctypes.c_double(0.0)
+        m = self.state_len
         self._check(self.lib.mf_film_solve_gradient(
-            self.h, n, ts, hs, it, ckpt_every, _dptr(g0), _dptr(warm0), _dptr(target), _dptr(work),
-            nb, _dptr(jcbar), kb, K if grad else 0, _dptr(wb), _dptr(hz_out), ctypes.byref(loss)))
+            self.h, n, ts, hs, it, ckpt_every, self._f64(g0, m, "g0"), self._f64(warm0, m, "warm0"),
+            self._f64(target, m, "target"), _dptr(work), nb, self._f64(jcbar, m, "jcbar"), kb,
+            K if grad else 0, self._f64(wb, m, "warm0_bar"), self._f64(hz_out, m, "hz_out"),
+            ctypes.byref(loss)))
         return loss.value, jcbar, (list(kb)[:K] if grad else None), wb
 
     def mf_set_jc_map(self, jc):
         """jc: device float64 tensor of the grid's cells."""
-        self._check(self.lib.mf_set_jc_map(self.h, _dptr(jc)))
+        self._check(self.lib.mf_set_jc_map(self.h, self._f64(jc, self.nx * self.ny * self.nz, "jc")))
 
     def mf_set_knot_values(self, values):
         v = [float(x) for x in values]
@@ -395,7 +435,9 @@ def mf_film_rhs_noalloc(problem: "Problem", t: float, y, ydot, force_iters: int 
     it = ctypes.c_int(0)
     msg = ctypes.create_string_buffer(256)
     s = stream if stream is not None else problem.stream
-    st = lib.mf_film_rhs_noalloc(ctypes.byref(problem.params), t, _dptr(y), _dptr(ydot),
+    n = problem.state_len
+    st = lib.mf_film_rhs_noalloc(ctypes.byref(problem.params), t, problem._f64(y, n, "y"),
+                                 problem._f64(ydot, n, "ydot"),
                                  force_iters, ctypes.c_void_p(s.cuda_stream), ctypes.byref(it),
                                  msg, 256)
     return st, it.value, msg.value.decode()

@@ -240,3 +240,24 @@ def test_step_and_state_round_trip():
     assert t1 >= 0.2
     info = p.mf_get_info()
     assert info["n_attempts"] == 1
+
+
+def test_binding_refuses_tensors_the_library_cannot_take():
+    """The C calls take bare pointers; the binding refuses, before any call, a tensor that is too
+    short, not float64, not contiguous or not on the problem's device."""
+    wl = film_workload(32, 32)
+    p = gpu_of(wl)
+    y = torch.zeros((32, 32), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        p.mf_rhs(0.1, y[:16], torch.zeros_like(y))
+    with pytest.raises(TypeError):
+        p.mf_rhs(0.1, y.float(), torch.zeros_like(y))
+    with pytest.raises(ValueError):
+        p.mf_rhs(0.1, y.t(), torch.zeros_like(y))                        # a transposed view
+    with pytest.raises(ValueError):
+        p.mf_set_state(0.0, y.cpu())
+    with pytest.raises(ValueError):
+        p.mf_readout(native.MF_READ_E, out=torch.zeros_like(y))          # e has 2 fields
+    with pytest.raises(ValueError):
+        p.mf_checkpoint_restore(torch.zeros(16, dtype=torch.uint8, device="cuda"))
+    assert p.mf_get_info()["n_rhs"] == 0
