@@ -148,3 +148,29 @@ def test_bean_slab_profile():
     assert np.all(np.sign(jy[layer]) == -np.sign(x[layer]))        # j_y = -d h_z / dx
     assert np.abs(jy[core]).max() < 0.5
     assert np.abs(jy[np.abs(x) > a + 0.1]).max() < 0.01            # no stray current outside
+
+
+def test_body_without_conductor_follows_the_applied_field():
+    """No superconductor: Eq. 18 adds to h_e_dot the field of the currents in Omega, and there are
+    none, so h_dot = h_e_dot along the applied direction on all of D, on the ramp and after its
+    knot; BS23 integrates that piecewise-constant rate exactly, so a ramp from h = 0 stays at
+    h_e(t) times the direction, and the moment stays 0."""
+    d = np.array([0.6, 0.0, 0.8])
+    wf = Waveform((0.0, 0.5, 1.0), (0.0, 0.25, 0.25))
+    p = _bulk(16, 1.0, mask=np.zeros((16, 16, 16), np.uint8), waveform=wf, he_dir=tuple(d),
+              iter_tol=1e-4)
+    h = 0.01 * W.rng(4).standard_normal((3, 16, 16, 16))
+    for t, rate in ((0.1, 0.5), (0.7, 0.0)):
+        hd, it, st = p.rhs(t, h)
+        assert st == OK
+        np.testing.assert_allclose(hd, np.broadcast_to(rate * d[:, None, None, None], hd.shape),
+                                   rtol=0, atol=1e-15)
+    p = _bulk(16, 1.0, mask=np.zeros((16, 16, 16), np.uint8), waveform=wf, he_dir=tuple(d),
+              iter_tol=1e-4)
+    s = BS23(p.rhs, wf, rtol=1e-6, atol=1e-6)
+    s.start(0.0, np.zeros((3, 16, 16, 16)), 1.0)
+    s.advance(1.0)
+    assert s.t == pytest.approx(1.0, abs=1e-15)
+    np.testing.assert_allclose(s.y, np.broadcast_to(0.25 * d[:, None, None, None], s.y.shape),
+                               rtol=0, atol=1e-14)
+    assert not p.magnetization(s.y).any()

@@ -212,3 +212,17 @@ def test_attempts_start_from_the_accepted_step():
     b, _, _ = q.rhs(s.t, s.y, None, 3)
     assert np.array_equal(a, b)
     assert p.attempt_first is False
+
+
+def test_film_without_conductor_is_the_applied_field():
+    """No superconductor, hence no sheet current: the field is the applied one everywhere, so the
+    outside iteration ends at h_dot = h_e_dot on all of D (Eq. 10 with nothing to shift, Eq. 11
+    with nothing to source) and f = 0 (g = 0 outside the film, reading 5); h_z = h_e."""
+    n, L = 32, 2.0
+    p = _film(n, n, L, L, np.zeros((n, n), np.uint8), waveform=Waveform((0.0, 1.0), (0.0, 0.5)))
+    g = 0.01 * W.rng(3).standard_normal((n, n))
+    for t in (0.1, 0.6):
+        gd, it, st = p.rhs(t, g)
+        assert st == OK and not gd.any()
+        np.testing.assert_allclose(p.last["hdot"], 0.5, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(p.hz(0.6, np.zeros((n, n))), 0.3, rtol=0, atol=1e-15)
